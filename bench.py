@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the cluster-TEBD iteration at chi_max = 1024 (cfg4 workload).
+
+Workload: the 500-qubit, 100-layer Clifford+T (20% T) random-structured
+circuit of the chi_max=1024 configuration (cutoff 1e-8, k_max 4,
+Q_max = 24), run from a synthetic saturated state: every interior bond at
+chi = 1024 (Haar-random right isometries, Porter-Thomas spectra), i.e. the
+regime in which the iteration spends its time.  A "step" is one cluster-TEBD
+iteration (partition + all cluster updates of the iteration, batched).  The
+metric is cluster updates (clusters with k >= 2) per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  For N > 1 (torchrun), every rank runs an
+independent replica (the path has no exchange step): value = units of all
+ranks / max time over ranks, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cluster updates/s and TFLOP/s (% TC peak) at χ=1024 vs plain FP64 GPU path"
+UNIT = "cluster updates/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp32_simt_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p or not os.path.exists(self.out):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def saturated_state(P, mps, n, chi, seed, device):
+    import torch
+
+    import synth
+    chis, sites, lams = synth.random_right_canonical_device(n, chi, seed, device=device,
+                                                            dtype=torch.complex64)
+    lam_arrays = [np.ascontiguousarray(l, dtype=np.float64) for l in lams]
+    mps.load_device(chis.astype(np.int32), [s.data_ptr() for s in sites],
+                    [l.ctypes.data for l in lam_arrays])
+    del sites
+    torch.cuda.empty_cache()
+    return chis
+
+
+def profile_rows(P, mps):
+    import ctypes as C
+    rows = np.zeros(4 * 32)
+    nk = C.c_int(0)
+    P._check(P.lib.ctebd_profile_read(mps._h, rows.ctypes.data_as(C.POINTER(C.c_double)), 32,
+                                      C.byref(nk)), "profile_read")
+    out = {}
+    for k in range(nk.value):
+        buf = C.create_string_buffer(64)
+        P.lib.ctebd_kernel_name(k, buf, 64)
+        out[buf.value.decode()] = dict(zip(("launches", "ms", "flops", "bytes"), rows[4 * k:4 * k + 4]))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# plain FP64 GPU comparator: complex128 merge / U / torch.linalg.svd, one
+# cluster at a time, no batching, no sketch (the path the target compares to)
+# ---------------------------------------------------------------------------
+def plain_fp64_update(torch, sites, lams, q0, k, U, chi_max, cutoff):
+    dev = sites[0].device
+    t = sites[q0].to(torch.complex128)
+    for j in range(1, k):
+        t = torch.tensordot(t, sites[q0 + j].to(torch.complex128), dims=([t.dim() - 1], [0]))
+    cl, cr = t.shape[0], t.shape[-1]
+    th = t.reshape(cl, 1 << k, cr)
+    Ut = torch.as_tensor(U, dtype=torch.complex128, device=dev)
+    th = torch.einsum("st,atb->asb", Ut, th)
+    lamL = torch.as_tensor(lams[q0], dtype=torch.float64, device=dev)
+    R = th.reshape(-1)
+    rdim = cr
+    fs = []
+    for j in range(k - 1, 0, -1):
+        m, n = cl << j, 2 * rdim
+        Mb = R.reshape(m, n)
+        w = lamL.repeat_interleave(1 << j).to(torch.complex128)
+        Usv, S, Vh = torch.linalg.svd(w[:, None] * Mb, full_matrices=False)
+        S2 = (S * S).double()
+        W = S2.sum()
+        tail = torch.flip(torch.cumsum(torch.flip(S2, [0]), 0), [0])
+        ok = tail <= cutoff * W
+        r = int(torch.nonzero(ok)[0].item()) if bool(ok.any()) else S.numel()
+        r = max(1, min(r, chi_max))
+        kept = S2[:r].sum()
+        fs.append(float(kept / W))
+        R = (Mb @ Vh[:r].conj().T / torch.sqrt(kept)).reshape(-1)
+        rdim = r
+    torch.cuda.synchronize()
+    return fs
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    device = f"cuda:{local_rank}"
+    stream = torch.cuda.Stream(device=device)
+    w = synth.WORKLOADS[4]
+    n, chi = args.n, args.chi
+    q_max = w.k_max + 2 * int(math.log2(chi))
+    cfg = P.make_config(n, chi, w.cutoff, q_max, 0, w.k_max, P.FP32, seed=4000 + rank)
+    c = synth.random_structured(n, w.n_layers, p1=w.p1, p2=w.p2, one_q=w.one_q, two_q=w.two_q,
+                                seed=4000 + rank)
+    circ = P.Circuit(n, c.gates, c.params)
+    mps = P.MPS(cfg, stream.cuda_stream)
+    saturated_state(P, mps, n, chi, seed=4000 + rank, device=device)
+
+    start = 0
+    totals = {"updates": 0, "dev_ms": 0.0, "wall_s": 0.0, "h2d": 0, "d2h": 0, "flops": 0.0}
+    step_f = []
+
+    def one_step(timed):
+        nonlocal start
+        if start >= circ.n_layers:
+            start = 0
+        t0 = time.perf_counter()
+        chi_now = mps.bond_dims()
+        clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, start, chi_now, cfg)
+        mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)
+        Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in clusters]
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        f = mps.step(clusters, Us)
+        ev1.record(stream)
+        chi_after = mps.bond_dims()          # device->host result read (bond dims, f)
+        ev1.synchronize()
+        t1 = time.perf_counter()
+        if timed:
+            totals["updates"] += len(clusters)
+            totals["dev_ms"] += ev0.elapsed_time(ev1)
+            totals["wall_s"] += t1 - t0
+            totals["h2d"] += sum(16 * U.size for U in Us)
+            totals["d2h"] += 8 * len(f) + 4 * len(chi_after)
+            step_f.append((len(clusters), sum(cl.k for cl in clusters), float(np.prod(f))))
+        start = stop
+        return clusters, Us
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    P._check(P.lib.ctebd_profile(mps._h, 1), "profile")
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            one_step(True)
+        torch.cuda.synchronize()
+    prof = profile_rows(P, mps)
+    P._check(P.lib.ctebd_profile(mps._h, 0), "profile")
+    res = dict(totals)
+    res["prof"] = prof
+    res["clocks"] = clk.summary()
+    res["steps_detail"] = step_f
+
+    # plain FP64 comparator on a sample of the next iteration's clusters
+    if rank == 0 and args.plain_sample > 0:
+        chi_now = mps.bond_dims()
+        clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, start, chi_now, cfg)
+        sample = clusters[: args.plain_sample]
+        sites = [torch.as_tensor(mps.site(q), device=device) for q in
+                 sorted({cl.q0 + j for cl in sample for j in range(cl.k)})]
+        idx = sorted({cl.q0 + j for cl in sample for j in range(cl.k)})
+        smap = {q: s for q, s in zip(idx, sites)}
+        lams = {cl.q0: mps.lam(cl.q0) for cl in sample}
+        Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in sample]
+        t0 = time.perf_counter()
+        fplain = []
+        for cl, U in zip(sample, Us):
+            fplain.append(plain_fp64_update(torch, smap, lams, cl.q0, cl.k, U, chi, w.cutoff))
+        t_plain = time.perf_counter() - t0
+        # ours on exactly the same sample, one launch batch
+        t0 = time.perf_counter()
+        fours = mps.step(sample, Us)
+        torch.cuda.synchronize()
+        t_ours = time.perf_counter() - t0
+        fp = np.concatenate([np.array(x) for x in fplain])
+        res["plain"] = {"updates": len(sample), "s": t_plain, "ours_s": t_ours,
+                        "max_abs_df": float(np.max(np.abs(fp - np.asarray(fours)))) if len(fp) == len(fours) else None,
+                        "F_plain": float(np.prod(fp)), "F_ours": float(np.prod(fours))}
+    return res
+
+
+def cpu_baseline(seconds=15.0, chi=128, nsites=16):
+    """Oracle (1 thread) on cluster updates of the cfg4 circuit over a reduced
+    chi synthetic state: full-size (chi=1024) oracle updates take ~1 h each."""
+    import oracle
+    import paper_2502_19289_gb300  # noqa: F401  (layering/partition come from the oracle)
+    import synth
+    w = synth.WORKLOADS[4]
+    c = synth.random_structured(nsites, w.n_layers, p1=w.p1, p2=w.p2, one_q=w.one_q,
+                                two_q=w.two_q, seed=4000)
+    layer, nl = oracle.asap_layers(nsites, c.gates)
+    chis, sites, lams = synth.random_right_canonical(nsites, chi, seed=4000)
+    m = oracle.MPS.from_arrays(sites, lams)
+    q_max = w.k_max + 2 * int(math.log2(chi))
+    done, t0, start = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds and start < nl:
+        clusters, stop = oracle.partition(nsites, c.gates, layer, nl, start, m.chi(), q_max, 0, w.k_max)
+        for q0, k in clusters:
+            U = oracle.cluster_unitary(q0, k, c, layer, start, stop)
+            m.cluster_update(q0, k, U, chi, w.cutoff)
+            done += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        start = stop
+    dt = time.perf_counter() - t0
+    v = done / dt
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} cluster updates (k=2..4) of the cfg4 circuit on a {nsites}-qubit "
+                      f"chi={chi} synthetic saturated state, 1 thread, {dt:.1f} s; chi=1024 oracle "
+                      "updates are ~1 h each",
+            "extrapolated_chi1024": v * (chi / 1024.0) ** 3}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=500)
+    ap.add_argument("--chi", type=int, default=1024)
+    ap.add_argument("--plain-sample", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    pk = peaks()
+    workload = (f"cfg4: n={args.n}, 100-layer random-structured Clifford+T (20% T), "
+                f"chi_max={args.chi}, cutoff 1e-8, k_max=4, Q_max={4 + 2 * int(math.log2(args.chi))}; "
+                "synthetic saturated state (all interior bonds at chi_max)")
+    config = {"workload": workload, "precision": "complex64 contractions, fp64 spectra/weights",
+              "l2": "inputs larger than L2 (theta/Gram per step >> 129 MB)", "replicas": world}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        for _ in range(args.warmup):
+            cpu_baseline(seconds=2.0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(cpu_baseline(seconds=max(args.cpu_seconds / max(args.steps, 1), 3.0)))
+        dt = time.perf_counter() - t0
+        v = float(np.mean([x["value"] for x in vals]))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": v},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    dev_s = res["dev_ms"] / 1000.0
+    units = res["updates"]
+    wall = res["wall_s"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s, wall], device=f"cuda:{local_rank}", dtype=torch.float64)
+        u = torch.tensor([units], device=f"cuda:{local_rank}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dev_s, wall = float(t[0]), float(t[1])
+        units = int(u[0])
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    prof = res["prof"]
+    clocks = res["clocks"]
+    sm = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    # dominant kernel class by device time
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    alu_peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    if dom["flops"] > 0:
+        achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1)}
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_source": pk["source"], "launches": dom["launches"]}
+    total_flops = sum(v["flops"] for v in prof.values())
+    tflops = total_flops / dev_s / 1e12 if dev_s > 0 else 0.0
+    gpu_launches = int(sum(v["launches"] for v in prof.values()))
+    value = units / dev_s if dev_s > 0 else 0.0
+    cpu = cpu_baseline(seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic (seeded circuit + random saturated MPS)", "config": config,
+        "tflops_algorithmic": tflops * world,
+        "tc_frac": None,
+        "roofline": roof,
+        "kernels": {k: {"launches": int(v["launches"]), "ms": round(v["ms"], 3),
+                        "share": round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4)}
+                    for k, v in prof.items() if v["launches"] > 0},
+        "cpu_baseline": cpu,
+        "e2e": {"value": units / wall if wall > 0 else 0.0, "unit": UNIT,
+                "h2d_bytes_per_step": int(res["h2d"] / max(args.steps, 1)),
+                "d2h_bytes_per_step": int(res["d2h"] / max(args.steps, 1))},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "updates": units,
+        "steps_detail": res["steps_detail"],
+    }
+    if "plain" in res:
+        pl = res["plain"]
+        line["plain_fp64"] = {"updates_per_s": pl["updates"] / pl["s"],
+                              "ours_same_sample_updates_per_s": pl["updates"] / pl["ours_s"],
+                              "speedup": (pl["s"] / pl["ours_s"]) if pl["ours_s"] > 0 else None,
+                              "max_abs_df": pl["max_abs_df"], "F_plain": pl["F_plain"],
+                              "F_ours": pl["F_ours"], "sample_updates": pl["updates"]}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

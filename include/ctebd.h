@@ -1,0 +1,213 @@
+/*
+ * ctebd.h -- C ABI of the GB300 cluster-TEBD cluster-update library.
+ *
+ * Method: arXiv 2502.19289, Sec. III.A (cluster-TEBD).  One iteration takes the
+ * circuit's gate list, partitions it into entanglement clusters up to a stop
+ * layer L* (Eqs. 6-8), contracts every cluster exactly -- the k MPS sites are
+ * merged into theta (chi_L, 2^k, chi_R) and the cluster's gates act as one
+ * 2^k x 2^k unitary -- and decomposes theta back into k sites by successive
+ * truncated SVDs (Fig. 2, Fig. 3), accumulating the fidelity product of
+ * Eqs. 4-5.
+ *
+ * Conventions
+ *   - Qubits 0..n-1, big-endian basis (qubit 0 is the most significant bit of
+ *     a basis-state index; |x> = |x_0> (x) |x_1> ..., Sec. IV.A).
+ *   - Bond b in 0..n sits left of qubit b; chi[0] = chi[n] = 1.
+ *   - Site q is a row-major complex tensor (chi[q], 2, chi[q+1]).  Complex
+ *     numbers are interleaved (re, im) pairs.  Host copies are complex128.
+ *   - The MPS is held in right-canonical (Vidal) form: right isometries B_q
+ *     plus the Schmidt spectrum lambda_b of every bond.  A cluster's theta is
+ *     diag(lambda_L) * B_q ... B_{q+k-1}, so every disjoint cluster of an
+ *     iteration is truncated against its own Schmidt weights independently.
+ *   - Gate matrices: App. A (plus S = P(pi/2)); the first listed qubit of a
+ *     two-qubit gate is the most significant bit of its 4x4 matrix.
+ *
+ * Ownership and errors
+ *   - Every call returns int status: CTEBD_OK (0) or a negative CTEBD_ERR_*.
+ *     ctebd_last_error() returns the message of the last failure in the
+ *     calling thread.
+ *   - The library owns all device memory of an mps handle.  The caller owns
+ *     every host array it passes and may pass a cudaStream_t (NULL: the
+ *     library creates its own stream).  Host results are returned only after
+ *     the work producing them has completed on that stream.
+ *   - No call falls back to a CPU implementation: a missing or failing GPU
+ *     returns CTEBD_ERR_CUDA.
+ */
+#ifndef CTEBD_ABI_H_
+#define CTEBD_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CTEBD_OK = 0,
+  CTEBD_ERR_ARG = -1,     /* invalid argument or precondition */
+  CTEBD_ERR_OOM = -2,     /* device or host allocation failed */
+  CTEBD_ERR_CUDA = -3,    /* CUDA runtime error (message has details) */
+  CTEBD_ERR_TIMEOUT = -4, /* a bounded device-side wait expired */
+  CTEBD_ERR_NUMERIC = -5, /* non-finite data or a factorisation that failed */
+  CTEBD_ERR_STATE = -6    /* call out of order (e.g. truncate_split without apply_cluster) */
+};
+
+/* Arithmetic of the contractions.  FP64: complex128 everywhere.  FP32:
+   complex64 sites and contractions, FP64 spectra, weights and fidelities. */
+enum { CTEBD_FP64 = 0, CTEBD_FP32 = 1 };
+
+/* Gate codes of the input format (App. A, plus S = P(pi/2) and C-P(phi)). */
+enum {
+  CTEBD_H = 1, CTEBD_X, CTEBD_Y, CTEBD_Z, CTEBD_S, CTEBD_T, CTEBD_P, CTEBD_X14, CTEBD_SQW,
+  CTEBD_CNOT = 10, CTEBD_CY, CTEBD_CZ, CTEBD_SWAP, CTEBD_CH, CTEBD_CS, CTEBD_CT,
+  CTEBD_SQSWAP, CTEBD_CP
+};
+
+/* Simulation parameters (Sec. II.B truncation, Eqs. 7-8 partition limits). */
+typedef struct {
+  int n_qubits;
+  int chi_max;        /* maximum bond dimension (Sec. II.B) */
+  double cutoff;      /* eta: discarded-weight cutoff, relative (0 = keep all) */
+  int q_max;          /* Eq. 7: log2 of the largest cluster tensor */
+  int l_max;          /* Eq. 8: max layers per iteration (<= 0: unbounded) */
+  int k_max;          /* max qubits per cluster (<= 0: only Eq. 7 limits) */
+  int precision;      /* CTEBD_FP64 | CTEBD_FP32 */
+  int sketch_oversample; /* p of the randomized range finder (0: default 16) */
+  int power_iters;    /* q of the randomized range finder */
+  int use_rank_model; /* 1: size sketches with the loaded rank predictor */
+  uint64_t seed;      /* counter-based RNG key of the sketch matrices */
+} ctebd_config;
+
+/* One gate.  layer is 1-based (Sec. II.A); assign_layers() fills it. */
+typedef struct {
+  int layer;
+  int n_q;            /* 1, 2 or 3 qubits, contiguous for n_q > 1 */
+  int q[3];
+  int kind;
+  double param;
+} ctebd_gate;
+
+/* One entanglement cluster: qubits q0..q0+k-1 (Sec. III.A). */
+typedef struct {
+  int q0;
+  int k;
+  int layer_lo;       /* gates with layer_lo < layer <= layer_hi belong to it */
+  int layer_hi;
+} ctebd_cluster;
+
+typedef struct ctebd_mps ctebd_mps;
+
+/* Create the product state |0...0> (all chi = 1, Sec. IV.A) on the current
+   CUDA device.  cuda_stream: a cudaStream_t or NULL.  Validates the Eq. 7/8
+   preconditions: k_max >= 2 (or <= 0), and q_max >= 2 + 2 log2(chi_max) so a
+   single layer of two-qubit gates always fits.  *out is owned by the caller
+   and released with mps_destroy.  Errors: ARG, OOM, CUDA. */
+int mps_create(const ctebd_config* cfg, void* cuda_stream, ctebd_mps** out);
+int mps_destroy(ctebd_mps* mps);
+
+/* Sec. II.A: assign every gate the earliest layer after the last gate on any
+   of its qubits (1-based).  Returns the number of layers in *n_layers.
+   Pure host function.  Errors: ARG (qubit out of range). */
+int assign_layers(ctebd_gate* gates, int n_gates, int n_qubits, int* n_layers);
+
+/* Sec. III.A, Eqs. 6-8: the clusters of one iteration starting after layer
+   layer_start.  chi: n_qubits+1 current bond dimensions.  The bond array is
+   grown layer by layer; the iteration stops at the last layer L* for which
+   every run of entangled bonds (cluster of k = run length + 1 qubits,
+   bounded by chi[q0] and chi[q0+k]) satisfies 2^k chi_L chi_R <= 2^q_max,
+   k <= k_max, and L* - layer_start <= l_max.  Writes up to cap clusters
+   (q0 ascending, layer_lo = layer_start, layer_hi = L*), *n_out and
+   *layer_stop = L*.  Pure host function, deterministic.
+   Errors: ARG (non-contiguous multi-qubit gate, cap too small),
+   STATE (no layer fits: preconditions violated). */
+int cluster_partition(const ctebd_gate* gates, int n_gates, int layer_start,
+                      const int* chi, const ctebd_config* cfg,
+                      ctebd_cluster* out, int cap, int* n_out, int* layer_stop);
+
+/* The exactly contracted cluster as one unitary: the ordered product of the
+   gates with layer_lo < layer <= layer_hi acting inside [q0, q0+k).  U is
+   written row-major 2^k x 2^k complex128 (q0 is the MSB).  Host function.
+   Errors: ARG (a gate straddles the window). */
+int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c, double* U);
+
+/* One-qubit gate on a qubit outside every cluster (applied to its site's
+   physical index; the paper is silent on such qubits).  u: 2x2 complex128
+   row-major host array.  Errors: ARG, CUDA. */
+int apply_1q(ctebd_mps* mps, int q, const double* u);
+
+/* All one-qubit gates of layers (layer_lo, layer_hi] on qubits outside the
+   n_clusters clusters, applied in layer order as one 2x2 product per qubit
+   (one batched launch).  Errors: ARG, CUDA. */
+int apply_singletons(ctebd_mps* mps, const ctebd_gate* gates, int n_gates,
+                     const ctebd_cluster* clusters, int n_clusters, int layer_lo, int layer_hi);
+
+/* Sec. III.A contraction of one cluster: theta = diag(lambda_L) B_q...B_{q+k-1}
+   with U (2^k x 2^k complex128, row-major, host) applied to its physical
+   multi-index.  theta stays on the device, pending truncate_split on the same
+   cluster.  Errors: ARG, CUDA, STATE (cluster already pending). */
+int apply_cluster(ctebd_mps* mps, const ctebd_cluster* c, const double* U);
+
+/* Fig. 2 / Fig. 3: split the pending theta of cluster c back into k sites by
+   k-1 truncated SVDs (right to left), truncation rule of Sec. II.B (chi_max
+   and the relative discarded-weight cutoff eta), per-split fidelity f_j of
+   Eq. 4 written to f_out[k-1] (may be NULL), product accumulated (Eq. 5).
+   Errors: STATE (nothing pending), CUDA, NUMERIC. */
+int truncate_split(ctebd_mps* mps, const ctebd_cluster* c, double* f_out);
+
+/* All clusters of one iteration, batched: every phase is one launch over all
+   n clusters.  U[i]: host pointer to cluster i's unitary.  f_out: per-split
+   fidelities, cluster by cluster (sum of k_i - 1 entries), may be NULL.
+   Clusters must be disjoint.  Errors: ARG, CUDA, NUMERIC. */
+int step(ctebd_mps* mps, const ctebd_cluster* c, int n, const double* const* U, double* f_out);
+
+/* Eq. 5: product of all per-split fidelities so far (FP64). */
+int fidelity(const ctebd_mps* mps, double* F);
+
+/* <bits|psi>: bits has n_qubits entries in {0,1}, qubit 0 first. */
+int amplitude(const ctebd_mps* mps, const uint8_t* bits, double* re, double* im);
+
+/* Current bond dimensions, n_qubits+1 entries. */
+int mps_bond_dims(const ctebd_mps* mps, int* chi);
+
+/* Copy site q to host as complex128 (chi[q]*2*chi[q+1] complex = 2x doubles);
+   cap is the capacity of buf in doubles.  Errors: ARG (cap too small). */
+int mps_to_host(const ctebd_mps* mps, int site, double* buf, size_t cap);
+
+/* Copy bond b's spectrum (chi[b] doubles). */
+int mps_lambda_to_host(const ctebd_mps* mps, int bond, double* buf, size_t cap);
+
+/* Replace the state: chi (n+1), sites[q] complex128 host arrays of
+   chi[q]*2*chi[q+1] complex, lambdas[b] host arrays of chi[b] doubles.
+   Sites must be right isometries (not checked). Errors: ARG, OOM, CUDA. */
+int mps_load(ctebd_mps* mps, const int* chi, const double* const* sites,
+             const double* const* lambdas);
+
+/* Same, from device buffers already in the run precision (complex64 for
+   FP32, complex128 for FP64), row-major; copies device-to-device. */
+int mps_load_device(ctebd_mps* mps, const int* chi, const void* const* sites,
+                    const double* const* lambdas);
+
+/* Per-split log of the last step() / truncate_split: rows of 8 doubles
+   (q0, k, bond, m, n, r, f, W).  *n_rows receives the row count; up to cap
+   rows are written. */
+int mps_split_log(const ctebd_mps* mps, double* rows, int cap, int* n_rows);
+
+/* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
+   and starts CUDA-event timing of every launch on the handle's stream (0
+   stops timing; launch counts and algorithmic flop/byte counts are always
+   kept).  ctebd_profile_read writes, per kernel class k < cap, the row
+   (launches, total ms, algorithmic flops, algorithmic bytes) at rows[4k]
+   and the number of classes in *n_kinds; ctebd_kernel_name names class k.
+   Not part of the paper: instrumentation of this implementation. */
+int ctebd_profile(ctebd_mps* mps, int mode);
+int ctebd_profile_read(ctebd_mps* mps, double* rows, int cap, int* n_kinds);
+int ctebd_kernel_name(int kind, char* buf, size_t n);
+
+/* Message of the last error in this thread (NUL-terminated, truncated to n). */
+int ctebd_last_error(char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTEBD_ABI_H_ */

@@ -1,0 +1,300 @@
+"""GB300 cluster-TEBD cluster update (arXiv 2502.19289, Sec. III.A).
+
+Thin ctypes binding of ``libctebd.so`` (C ABI in ``include/ctebd.h``).  This
+module only marshals arguments: partition, cluster unitaries, contraction,
+truncated splits and observables all run inside the library (host C++ for the
+partition and unitaries, CUDA kernels for everything on the state).  There is
+no CPU fallback: importing this package without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctebd.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32 = 0, 1
+
+
+class CtebdError(RuntimeError):
+    pass
+
+
+class Config(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("chi_max", C.c_int), ("cutoff", C.c_double),
+                ("q_max", C.c_int), ("l_max", C.c_int), ("k_max", C.c_int),
+                ("precision", C.c_int), ("sketch_oversample", C.c_int),
+                ("power_iters", C.c_int), ("use_rank_model", C.c_int), ("seed", C.c_uint64)]
+
+
+class Gate(C.Structure):
+    _fields_ = [("layer", C.c_int), ("n_q", C.c_int), ("q", C.c_int * 3), ("kind", C.c_int),
+                ("param", C.c_double)]
+
+
+class Cluster(C.Structure):
+    _fields_ = [("q0", C.c_int), ("k", C.c_int), ("layer_lo", C.c_int), ("layer_hi", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python paper_2502_19289_gb300/build.py` "
+            "(nvcc, sm_103a). There is no CPU fallback.")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    sig = {
+        "mps_create": [C.POINTER(Config), P, C.POINTER(P)],
+        "mps_destroy": [P],
+        "assign_layers": [C.POINTER(Gate), I, I, C.POINTER(I)],
+        "cluster_partition": [C.POINTER(Gate), I, I, C.POINTER(I), C.POINTER(Config),
+                              C.POINTER(Cluster), I, C.POINTER(I), C.POINTER(I)],
+        "cluster_unitary": [C.POINTER(Gate), I, C.POINTER(Cluster), C.POINTER(D)],
+        "apply_1q": [P, I, C.POINTER(D)],
+        "apply_singletons": [P, C.POINTER(Gate), I, C.POINTER(Cluster), I, I, I],
+        "apply_cluster": [P, C.POINTER(Cluster), C.POINTER(D)],
+        "truncate_split": [P, C.POINTER(Cluster), C.POINTER(D)],
+        "step": [P, C.POINTER(Cluster), I, C.POINTER(C.POINTER(D)), C.POINTER(D)],
+        "fidelity": [P, C.POINTER(D)],
+        "amplitude": [P, C.POINTER(C.c_uint8), C.POINTER(D), C.POINTER(D)],
+        "mps_bond_dims": [P, C.POINTER(I)],
+        "mps_to_host": [P, I, C.POINTER(D), S],
+        "mps_lambda_to_host": [P, I, C.POINTER(D), S],
+        "mps_load": [P, C.POINTER(I), C.POINTER(C.POINTER(D)), C.POINTER(C.POINTER(D))],
+        "mps_load_device": [P, C.POINTER(I), C.POINTER(P), C.POINTER(P)],
+        "mps_split_log": [P, C.POINTER(D), I, C.POINTER(I)],
+        "ctebd_last_error": [C.c_char_p, S],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    _lib.ctebd_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise CtebdError(f"{what} failed ({rc}): {last_error()}")
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def make_config(n_qubits, chi_max, cutoff, q_max, l_max=0, k_max=0, precision=FP32,
+                sketch_oversample=16, power_iters=1, use_rank_model=0, seed=1234) -> Config:
+    return Config(n_qubits, chi_max, cutoff, q_max, l_max, k_max, precision,
+                  sketch_oversample, power_iters, use_rank_model, seed)
+
+
+def gates_from_arrays(gates5: np.ndarray, params: np.ndarray):
+    """Input-format gate rows (n_q, q0, q1, q2, kind) -> ctebd_gate array."""
+    g = np.asarray(gates5, dtype=np.int32).reshape(-1, 5)
+    arr = (Gate * max(len(g), 1))()
+    for i, (nq, a, b, c, kind) in enumerate(g):
+        arr[i].layer = 0
+        arr[i].n_q = int(nq)
+        arr[i].q[0], arr[i].q[1], arr[i].q[2] = int(a), int(b), int(c)
+        arr[i].kind = int(kind)
+        arr[i].param = float(params[i])
+    return arr, len(g)
+
+
+def assign_layers(gates, n_gates, n_qubits) -> int:
+    nl = C.c_int(0)
+    _check(_lib.assign_layers(gates, n_gates, n_qubits, C.byref(nl)), "assign_layers")
+    return nl.value
+
+
+def cluster_partition(gates, n_gates, layer_start, chi, cfg: Config):
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    cap = max(cfg.n_qubits, 1)
+    out = (Cluster * cap)()
+    n_out, stop = C.c_int(0), C.c_int(0)
+    _check(_lib.cluster_partition(gates, n_gates, layer_start, _ip(chi), C.byref(cfg), out, cap,
+                                  C.byref(n_out), C.byref(stop)), "cluster_partition")
+    return [out[i] for i in range(n_out.value)], stop.value
+
+
+def cluster_unitary(gates, n_gates, cl: Cluster) -> np.ndarray:
+    D = 1 << cl.k
+    U = np.zeros(2 * D * D)
+    _check(_lib.cluster_unitary(gates, n_gates, C.byref(cl), _dp(U)), "cluster_unitary")
+    return U.view(np.complex128).reshape(D, D)
+
+
+class MPS:
+    """Device MPS handle (right-canonical sites + bond spectra)."""
+
+    def __init__(self, cfg: Config, stream=None):
+        self.cfg = cfg
+        self.n = cfg.n_qubits
+        h = C.c_void_p()
+        _check(_lib.mps_create(C.byref(cfg), C.c_void_p(stream or 0), C.byref(h)), "mps_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mps_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- state access ---------------------------------------------------
+    def bond_dims(self) -> np.ndarray:
+        chi = np.zeros(self.n + 1, dtype=np.int32)
+        _check(_lib.mps_bond_dims(self._h, _ip(chi)), "mps_bond_dims")
+        return chi
+
+    def site(self, q: int) -> np.ndarray:
+        chi = self.bond_dims()
+        buf = np.zeros(2 * chi[q] * 2 * chi[q + 1])
+        _check(_lib.mps_to_host(self._h, q, _dp(buf), buf.size), "mps_to_host")
+        return buf.view(np.complex128).reshape(chi[q], 2, chi[q + 1])
+
+    def lam(self, b: int) -> np.ndarray:
+        chi = self.bond_dims()
+        buf = np.zeros(max(chi[b], 1))
+        _check(_lib.mps_lambda_to_host(self._h, b, _dp(buf), buf.size), "mps_lambda_to_host")
+        return buf[: chi[b]]
+
+    def load(self, chi, sites, lams):
+        chi = np.ascontiguousarray(chi, dtype=np.int32)
+        s = [np.ascontiguousarray(x, dtype=np.complex128).view(np.float64).reshape(-1) for x in sites]
+        l = [np.ascontiguousarray(x, dtype=np.float64) for x in lams]
+        sp = (C.POINTER(C.c_double) * len(s))(*[_dp(x) for x in s])
+        lp = (C.POINTER(C.c_double) * len(l))(*[_dp(x) for x in l])
+        _check(_lib.mps_load(self._h, _ip(chi), sp, lp), "mps_load")
+
+    def load_device(self, chi, site_ptrs, lam_ptrs):
+        chi = np.ascontiguousarray(chi, dtype=np.int32)
+        sp = (C.c_void_p * len(site_ptrs))(*site_ptrs)
+        lp = (C.c_void_p * len(lam_ptrs))(*lam_ptrs)
+        _check(_lib.mps_load_device(self._h, _ip(chi), sp, lp), "mps_load_device")
+
+    def fidelity(self) -> float:
+        F = C.c_double(0)
+        _check(_lib.fidelity(self._h, C.byref(F)), "fidelity")
+        return F.value
+
+    def amplitude(self, bits) -> complex:
+        b = np.ascontiguousarray(bits, dtype=np.uint8)
+        re, im = C.c_double(0), C.c_double(0)
+        _check(_lib.amplitude(self._h, b.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(re),
+                              C.byref(im)), "amplitude")
+        return complex(re.value, im.value)
+
+    def split_log(self) -> np.ndarray:
+        n = C.c_int(0)
+        _check(_lib.mps_split_log(self._h, None, 0, C.byref(n)), "mps_split_log")
+        rows = np.zeros(8 * max(n.value, 1))
+        _check(_lib.mps_split_log(self._h, _dp(rows), n.value, C.byref(n)), "mps_split_log")
+        return rows[: 8 * n.value].reshape(-1, 8)
+
+    # --- the cluster update ----------------------------------------------
+    def apply_1q(self, q: int, u: np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.complex128).view(np.float64).reshape(-1)
+        _check(_lib.apply_1q(self._h, q, _dp(u)), "apply_1q")
+
+    def apply_singletons(self, gates, n_gates, clusters, lo, hi):
+        arr = (Cluster * max(len(clusters), 1))(*clusters)
+        _check(_lib.apply_singletons(self._h, gates, n_gates, arr, len(clusters), lo, hi),
+               "apply_singletons")
+
+    def apply_cluster(self, cl: Cluster, U: np.ndarray):
+        U = np.ascontiguousarray(U, dtype=np.complex128).view(np.float64).reshape(-1)
+        _check(_lib.apply_cluster(self._h, C.byref(cl), _dp(U)), "apply_cluster")
+
+    def truncate_split(self, cl: Cluster) -> np.ndarray:
+        f = np.zeros(max(cl.k - 1, 1))
+        _check(_lib.truncate_split(self._h, C.byref(cl), _dp(f)), "truncate_split")
+        return f[: cl.k - 1]
+
+    def step(self, clusters, Us) -> np.ndarray:
+        n = len(clusters)
+        arr = (Cluster * max(n, 1))(*clusters)
+        Uf = [np.ascontiguousarray(U, dtype=np.complex128).view(np.float64).reshape(-1) for U in Us]
+        up = (C.POINTER(C.c_double) * max(n, 1))(*[_dp(u) for u in Uf])
+        f = np.zeros(max(sum(c.k - 1 for c in clusters), 1))
+        _check(_lib.step(self._h, arr, n, up, _dp(f)), "step")
+        return f[: sum(c.k - 1 for c in clusters)]
+
+
+# C-style aliases with the ABI's names
+def mps_create(cfg: Config, stream=None) -> MPS:
+    return MPS(cfg, stream)
+
+
+def apply_cluster(mps: MPS, cl: Cluster, U):
+    return mps.apply_cluster(cl, U)
+
+
+def truncate_split(mps: MPS, cl: Cluster):
+    return mps.truncate_split(cl)
+
+
+def step(mps: MPS, clusters, Us):
+    return mps.step(clusters, Us)
+
+
+def fidelity(mps: MPS) -> float:
+    return mps.fidelity()
+
+
+def amplitude(mps: MPS, bits) -> complex:
+    return mps.amplitude(bits)
+
+
+class Circuit:
+    """A circuit in the library's gate format, layered (Sec. II.A)."""
+
+    def __init__(self, n_qubits: int, gates5, params):
+        self.n = n_qubits
+        self.gates, self.n_gates = gates_from_arrays(gates5, params)
+        self.n_layers = assign_layers(self.gates, self.n_gates, n_qubits)
+
+
+def run_iteration(mps: MPS, circ: Circuit, start: int):
+    """One cluster-TEBD iteration (Sec. III.A) from layer ``start``.
+
+    Returns (clusters, stop layer, per-split fidelities)."""
+    chi = mps.bond_dims()
+    clusters, stop = cluster_partition(circ.gates, circ.n_gates, start, chi, mps.cfg)
+    mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)
+    Us = [cluster_unitary(circ.gates, circ.n_gates, c) for c in clusters]
+    f = mps.step(clusters, Us) if clusters else np.zeros(0)
+    return clusters, stop, f
+
+
+def simulate(circ: Circuit, cfg: Config, stream=None, callback=None) -> MPS:
+    """Cluster-TEBD from |0...0> over the whole circuit (Sec. III.A loop)."""
+    mps = MPS(cfg, stream)
+    start = 0
+    while start < circ.n_layers:
+        clusters, stop, f = run_iteration(mps, circ, start)
+        if callback:
+            callback(start, stop, clusters, f)
+        start = stop
+    return mps

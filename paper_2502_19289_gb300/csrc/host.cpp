@@ -1,0 +1,1129 @@
+// host.cpp -- C ABI entry points and host orchestration of the cluster update.
+//
+// Host-side pieces (bit-exact, deterministic): earliest-layer assignment
+// (Sec. II.A), the cluster partition with the Eq. 7 / Eq. 8 stop rule
+// (Sec. III.A), gate matrices (App. A) and the cluster unitaries.  The device
+// pieces (merge, U, Gram, eigen-solve, truncation, write-back) are launched
+// here, batched over all clusters of an iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ctebd.h"
+#include "internal.h"
+
+using namespace ctebd;
+using cd = std::complex<double>;
+
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(CTEBD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+  } while (0)
+#define TRY(call)              \
+  do {                         \
+    int rc_ = (call);          \
+    if (rc_ != CTEBD_OK) return rc_; \
+  } while (0)
+
+extern "C" int ctebd_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return CTEBD_ERR_ARG;
+  std::snprintf(buf, n, "%s", g_err.c_str());
+  return CTEBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// App. A gate matrices (row-major, first listed qubit = MSB / control)
+// ---------------------------------------------------------------------------
+static int gate_dim(int kind, double param, cd* g) {
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const cd i1(0, 1), w8 = std::polar(1.0, M_PI / 4);
+  auto set2 = [&](cd a, cd b, cd c, cd d) { g[0] = a; g[1] = b; g[2] = c; g[3] = d; return 2; };
+  switch (kind) {
+    case CTEBD_H: return set2(r2, r2, r2, -r2);
+    case CTEBD_X: return set2(0., 1., 1., 0.);
+    case CTEBD_Y: return set2(0., -i1, i1, 0.);
+    case CTEBD_Z: return set2(1., 0., 0., -1.);
+    case CTEBD_S: return set2(1., 0., 0., i1);
+    case CTEBD_T: return set2(1., 0., 0., w8);
+    case CTEBD_P: return set2(1., 0., 0., std::polar(1.0, param));
+    case CTEBD_X14: {
+      const cd ph = std::polar(1.0, M_PI / 8);
+      const double c = std::cos(M_PI / 8), s = std::sin(M_PI / 8);
+      return set2(ph * c, -i1 * ph * s, -i1 * ph * s, ph * c);
+    }
+    case CTEBD_SQW: return set2(r2 * w8, -i1 * r2, r2, r2 * w8);  // principal root of (X+Y)/sqrt2
+    default: break;
+  }
+  for (int i = 0; i < 16; i++) g[i] = 0;
+  for (int i = 0; i < 4; i++) g[5 * i] = 1;
+  switch (kind) {
+    case CTEBD_CNOT: g[10] = 0; g[15] = 0; g[11] = 1; g[14] = 1; return 4;
+    case CTEBD_CY: g[10] = 0; g[15] = 0; g[11] = -i1; g[14] = i1; return 4;
+    case CTEBD_CZ: g[15] = -1; return 4;
+    case CTEBD_SWAP: g[5] = 0; g[10] = 0; g[6] = 1; g[9] = 1; return 4;
+    case CTEBD_CH: g[10] = r2; g[11] = r2; g[14] = r2; g[15] = -r2; return 4;
+    case CTEBD_CS: g[15] = i1; return 4;
+    case CTEBD_CT: g[15] = w8; return 4;
+    case CTEBD_CP: g[15] = std::polar(1.0, param); return 4;
+    case CTEBD_SQSWAP:
+      g[5] = 0.5 * (1. + i1); g[6] = 0.5 * (1. - i1); g[9] = 0.5 * (1. - i1); g[10] = 0.5 * (1. + i1);
+      return 4;
+    default: return 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. II.A layering, Sec. III.A partition
+// ---------------------------------------------------------------------------
+extern "C" int assign_layers(ctebd_gate* gates, int n_gates, int n_qubits, int* n_layers) {
+  if (n_gates < 0 || n_qubits <= 0 || (n_gates > 0 && !gates)) return fail(CTEBD_ERR_ARG, "assign_layers: bad args");
+  std::vector<int> last(n_qubits, 0);
+  int nl = 0;
+  for (int i = 0; i < n_gates; i++) {
+    ctebd_gate& g = gates[i];
+    if (g.n_q < 1 || g.n_q > 3) return fail(CTEBD_ERR_ARG, "assign_layers: n_q out of range");
+    int L = 0;
+    for (int t = 0; t < g.n_q; t++) {
+      if (g.q[t] < 0 || g.q[t] >= n_qubits) return fail(CTEBD_ERR_ARG, "assign_layers: qubit out of range");
+      L = std::max(L, last[g.q[t]]);
+    }
+    g.layer = L + 1;
+    for (int t = 0; t < g.n_q; t++) last[g.q[t]] = g.layer;
+    nl = std::max(nl, g.layer);
+  }
+  if (n_layers) *n_layers = nl;
+  return CTEBD_OK;
+}
+
+// A run of entangled bonds [b1, b2] is a cluster of qubits b1-1..b2 (Eq. 6:
+// 2^k chi[b1-1] chi[b2+1] with k = b2 - b1 + 2).
+static bool clusters_fit(const std::vector<char>& bond, int n, const int* chi, int q_max, int k_max) {
+  int b = 1;
+  while (b <= n - 1) {
+    if (!bond[b]) { ++b; continue; }
+    const int b1 = b;
+    while (b <= n - 1 && bond[b]) ++b;
+    const int k = b - b1 + 1;
+    if (k_max > 0 && k > k_max) return false;
+    // log2(2^k chi_L chi_R) <= q_max, compared exactly in integers
+    if (k > q_max) return false;
+    const unsigned long long budget = q_max - k >= 63 ? ~0ULL : (1ULL << (q_max - k));
+    const unsigned long long cl = (unsigned long long)chi[b1 - 1], cr = (unsigned long long)chi[b];
+    if (cl > budget || cr > budget / cl) return false;
+  }
+  return true;
+}
+
+extern "C" int cluster_partition(const ctebd_gate* gates, int n_gates, int layer_start, const int* chi,
+                                 const ctebd_config* cfg, ctebd_cluster* out, int cap, int* n_out,
+                                 int* layer_stop) {
+  if (!cfg || !chi || !n_out || !layer_stop || n_gates < 0 || (n_gates && !gates))
+    return fail(CTEBD_ERR_ARG, "cluster_partition: null argument");
+  const int n = cfg->n_qubits;
+  int n_layers = 0;
+  for (int i = 0; i < n_gates; i++) n_layers = std::max(n_layers, gates[i].layer);
+  // bucket gates by layer once
+  std::vector<int> order(n_gates);
+  for (int i = 0; i < n_gates; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+  std::vector<char> bond(n + 1, 0), tent;
+  int stop = layer_start;
+  size_t pos = std::lower_bound(order.begin(), order.end(), layer_start + 1,
+                                [&](int gi, int L) { return gates[gi].layer < L; }) - order.begin();
+  for (int L = layer_start + 1; L <= n_layers; L++) {
+    if (cfg->l_max > 0 && L - layer_start > cfg->l_max) break;
+    tent = bond;
+    while (pos < order.size() && gates[order[pos]].layer == L) {
+      const ctebd_gate& g = gates[order[pos++]];
+      if (g.n_q < 2) continue;
+      int lo = g.q[0], hi = g.q[0];
+      for (int t = 1; t < g.n_q; t++) { lo = std::min(lo, g.q[t]); hi = std::max(hi, g.q[t]); }
+      if (hi - lo != g.n_q - 1 || lo < 0 || hi >= n)
+        return fail(CTEBD_ERR_ARG, "cluster_partition: multi-qubit gate on non-adjacent qubits (route it first)");
+      for (int b = lo + 1; b <= hi; b++) tent[b] = 1;
+    }
+    if (!clusters_fit(tent, n, chi, cfg->q_max, cfg->k_max)) break;
+    bond.swap(tent);
+    stop = L;
+  }
+  if (stop == layer_start && layer_start < n_layers)
+    return fail(CTEBD_ERR_STATE, "cluster_partition: no layer fits Q_max / k_max (check preconditions)");
+  int nc = 0, b = 1;
+  while (b <= n - 1) {
+    if (!bond[b]) { ++b; continue; }
+    const int b1 = b;
+    while (b <= n - 1 && bond[b]) ++b;
+    if (nc < cap && out) {
+      out[nc].q0 = b1 - 1;
+      out[nc].k = b - b1 + 1;
+      out[nc].layer_lo = layer_start;
+      out[nc].layer_hi = stop;
+    }
+    ++nc;
+  }
+  *n_out = nc;
+  *layer_stop = stop;
+  if (nc > cap) return fail(CTEBD_ERR_ARG, "cluster_partition: cap too small");
+  return CTEBD_OK;
+}
+
+// apply a gate to a k-qubit state vector (local qubits, MSB = position 0)
+static void gate_on_vec(int k, cd* v, int gnq, const int* lq, const cd* g) {
+  const int dim = 1 << gnq;
+  long long mask = 0;
+  int pos[3];
+  for (int t = 0; t < gnq; t++) { pos[t] = k - 1 - lq[t]; mask |= 1LL << pos[t]; }
+  cd in[8], outv[8];
+  long long idx[8];
+  for (long long base = 0; base < (1LL << k); base++) {
+    if (base & mask) continue;
+    for (int x = 0; x < dim; x++) {
+      long long i = base;
+      for (int t = 0; t < gnq; t++) if ((x >> (gnq - 1 - t)) & 1) i |= 1LL << pos[t];
+      idx[x] = i;
+      in[x] = v[i];
+    }
+    for (int a = 0; a < dim; a++) {
+      cd s = 0;
+      for (int c = 0; c < dim; c++) s += g[a * dim + c] * in[c];
+      outv[a] = s;
+    }
+    for (int x = 0; x < dim; x++) v[idx[x]] = outv[x];
+  }
+}
+
+extern "C" int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c, double* U) {
+  if (!c || !U || c->k < 1 || c->k > 12) return fail(CTEBD_ERR_ARG, "cluster_unitary: bad args");
+  const int k = c->k;
+  const long long D = 1LL << k;
+  std::vector<cd> M(D * D, 0.0), col(D);
+  for (long long i = 0; i < D; i++) M[i * D + i] = 1;
+  std::vector<int> order;
+  for (int i = 0; i < n_gates; i++)
+    if (gates[i].layer > c->layer_lo && gates[i].layer <= c->layer_hi) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+  for (int gi : order) {
+    const ctebd_gate& g = gates[gi];
+    int lq[3], inside = 0;
+    for (int t = 0; t < g.n_q; t++) {
+      lq[t] = g.q[t] - c->q0;
+      inside += (lq[t] >= 0 && lq[t] < k);
+    }
+    if (!inside) continue;
+    if (inside != g.n_q) return fail(CTEBD_ERR_ARG, "cluster_unitary: gate straddles the cluster");
+    cd gm[16];
+    const int d = gate_dim(g.kind, g.param, gm);
+    if (!d || (d == 2) != (g.n_q == 1)) return fail(CTEBD_ERR_ARG, "cluster_unitary: unknown gate kind");
+    for (long long cI = 0; cI < D; cI++) {
+      for (long long r = 0; r < D; r++) col[r] = M[r * D + cI];
+      gate_on_vec(k, col.data(), g.n_q, lq, gm);
+      for (long long r = 0; r < D; r++) M[r * D + cI] = col[r];
+    }
+  }
+  for (long long i = 0; i < D * D; i++) { U[2 * i] = M[i].real(); U[2 * i + 1] = M[i].imag(); }
+  return CTEBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device staging of small descriptor arrays (pinned host -> device, bump)
+// ---------------------------------------------------------------------------
+struct Staging {
+  unsigned char* h = nullptr;
+  unsigned char* d = nullptr;
+  size_t cap = 0, off = 0;
+  cudaStream_t s = nullptr;
+  int init(size_t c, cudaStream_t st) {
+    s = st;
+    cap = c;
+    CUDA_TRY(cudaMallocHost(&h, cap));
+    CUDA_TRY(cudaMalloc(&d, cap));
+    return CTEBD_OK;
+  }
+  void release() {
+    if (h) cudaFreeHost(h);
+    if (d) cudaFree(d);
+    h = d = nullptr;
+  }
+  // Callers reset only after a stream synchronisation.
+  void reset() { off = 0; }
+  template <typename T>
+  int push(const T* src, size_t count, const T** out) {
+    const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (off + need > cap) {
+      CUDA_TRY(cudaStreamSynchronize(s));
+      off = 0;
+      if (need > cap) return fail(CTEBD_ERR_OOM, "staging buffer too small");
+    }
+    std::memcpy(h + off, src, sizeof(T) * count);
+    CUDA_TRY(cudaMemcpyAsync(d + off, h + off, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+    *out = reinterpret_cast<const T*>(d + off);
+    off += need;
+    return CTEBD_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// MPS handle
+// ---------------------------------------------------------------------------
+struct Work {
+  int q0, k, chiL, chiR;
+  void* bufA = nullptr;  // theta' / Mbar / remainder
+  void* bufB = nullptr;  // merge ping-pong / Mbar*V
+  size_t bufElems = 0;
+  void* G = nullptr;
+  void* V = nullptr;
+  void* J = nullptr;
+  size_t eigElems = 0, jElems = 0;
+  double* rho = nullptr;
+  int* perm = nullptr;
+  double* res = nullptr;
+  size_t nmax = 0;
+  int rdim = 0;          // current right dimension during splitting
+  bool owned = false;    // buffers allocated individually (apply_cluster path)
+};
+
+// ---------------------------------------------------------------------------
+// Per-kernel-class CUDA-event timing on the library's stream (off by
+// default) and launch counting (always on).  Flops and bytes are the
+// algorithmic amounts of each launch (complex MAC = 8 real flops).
+// ---------------------------------------------------------------------------
+enum KernelKind {
+  KK_GEMM_MERGE, KK_GEMM_U, KK_GEMM_GRAM, KK_GEMM_PROJ, KK_EIG_INIT, KK_EIG_INNER, KK_EIG_APPLY,
+  KK_COLNORM, KK_SELECT, KK_GATHER, KK_ONEQ, KK_AMP, KK_COUNT
+};
+static const char* kKindNames[KK_COUNT] = {
+  "gemm_merge", "gemm_apply_u", "gemm_gram", "gemm_project", "eig_init", "eig_inner", "eig_apply",
+  "colnorm", "select", "gather", "apply_1q", "amplitude"};
+
+struct Prof {
+  bool on = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double launches[KK_COUNT] = {0}, ms[KK_COUNT] = {0}, flops[KK_COUNT] = {0}, bytes[KK_COUNT] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void reset() {
+    for (int i = 0; i < KK_COUNT; i++) launches[i] = ms[i] = flops[i] = bytes[i] = 0;
+  }
+  // fold finished records into the accumulators (caller synchronised)
+  void drain() {
+    for (auto& r : recs) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.kind] += t;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  void release() {
+    drain();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
+struct ProfScope {
+  Prof& p;
+  cudaStream_t s;
+  int kind;
+  cudaEvent_t b = nullptr;
+  ProfScope(Prof& pr, cudaStream_t st, int k, double fl, double by) : p(pr), s(st), kind(k) {
+    p.launches[k] += 1;
+    p.flops[k] += fl;
+    p.bytes[k] += by;
+    if (p.on) {
+      cudaEvent_t a = p.get();
+      b = p.get();
+      cudaEventRecord(a, s);
+      p.recs.push_back({k, a, b});
+    }
+  }
+  ~ProfScope() {
+    if (b) cudaEventRecord(b, s);
+  }
+};
+
+struct ctebd_mps {
+  ctebd_config cfg{};
+  int n = 0;
+  bool fp64 = true;
+  size_t esz = 16;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<int> chi;
+  std::vector<void*> site;
+  std::vector<size_t> site_cap;
+  std::vector<double*> lam;
+  int lam_cap = 0;
+  double logF = 0;
+  std::vector<double> splitlog;
+  void* arena = nullptr;
+  size_t arena_cap = 0;
+  Staging stage;
+  double* h_res = nullptr;       // pinned results of select (4 per problem)
+  size_t h_res_cap = 0;
+  std::map<int, Work> pending;
+  Prof prof;
+};
+
+static int ensure_site(ctebd_mps* m, int q, size_t elems) {
+  if (m->site_cap[q] >= elems) return CTEBD_OK;
+  if (m->site[q]) CUDA_TRY(cudaFreeAsync(m->site[q], m->stream));
+  m->site[q] = nullptr;
+  CUDA_TRY(cudaMallocAsync(&m->site[q], std::max<size_t>(elems, 1) * m->esz, m->stream));
+  m->site_cap[q] = elems;
+  return CTEBD_OK;
+}
+
+extern "C" int mps_create(const ctebd_config* cfg, void* cuda_stream, ctebd_mps** out) {
+  if (!cfg || !out) return fail(CTEBD_ERR_ARG, "mps_create: null argument");
+  if (cfg->n_qubits < 1 || cfg->chi_max < 1 || cfg->chi_max > 2048)
+    return fail(CTEBD_ERR_ARG, "mps_create: n_qubits >= 1 and 1 <= chi_max <= 2048 required");
+  if (cfg->precision != CTEBD_FP64 && cfg->precision != CTEBD_FP32)
+    return fail(CTEBD_ERR_ARG, "mps_create: precision must be CTEBD_FP64 or CTEBD_FP32");
+  if (cfg->k_max == 1) return fail(CTEBD_ERR_ARG, "mps_create: k_max must be >= 2 (or <= 0)");
+  int lg = 0;
+  while ((1 << lg) < cfg->chi_max) lg++;
+  if (cfg->q_max < 2 + 2 * lg)
+    return fail(CTEBD_ERR_ARG, "mps_create: q_max >= 2 + 2 log2(chi_max) required (Eq. 7 must admit one layer)");
+  if (!(cfg->cutoff >= 0.0) || cfg->cutoff >= 1.0) return fail(CTEBD_ERR_ARG, "mps_create: 0 <= cutoff < 1");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(CTEBD_ERR_CUDA, "mps_create: no CUDA device");
+  ctebd_mps* m = new ctebd_mps();
+  m->cfg = *cfg;
+  m->n = cfg->n_qubits;
+  m->fp64 = cfg->precision == CTEBD_FP64;
+  m->esz = m->fp64 ? 16 : 8;
+  if (cuda_stream) {
+    m->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete m;
+      return fail(CTEBD_ERR_CUDA, "mps_create: stream");
+    }
+    m->own_stream = true;
+  }
+  m->chi.assign(m->n + 1, 1);
+  m->site.assign(m->n, nullptr);
+  m->site_cap.assign(m->n, 0);
+  m->lam_cap = cfg->chi_max;
+  m->lam.assign(m->n + 1, nullptr);
+  int rc = m->stage.init(8 << 20, m->stream);
+  if (rc) { mps_destroy(m); return rc; }
+  if (cudaMallocHost(&m->h_res, 4 * sizeof(double) * 4096) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "pinned"); }
+  m->h_res_cap = 4096;
+  std::vector<double> one(1, 1.0);
+  for (int b = 0; b <= m->n; b++) {
+    if (cudaMalloc(&m->lam[b], sizeof(double) * m->lam_cap) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "lambda"); }
+    cudaMemcpyAsync(m->lam[b], one.data(), sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  }
+  // |0> on every site: (1, 2, 1) tensor [1, 0]
+  std::vector<double> zero_state(4, 0.0);
+  zero_state[0] = 1.0;
+  for (int q = 0; q < m->n; q++) {
+    if (ensure_site(m, q, 2) != CTEBD_OK) { mps_destroy(m); return CTEBD_ERR_OOM; }
+    if (m->fp64) {
+      cudaMemcpyAsync(m->site[q], zero_state.data(), 32, cudaMemcpyHostToDevice, m->stream);
+    } else {
+      float z[4] = {1.f, 0.f, 0.f, 0.f};
+      cudaMemcpyAsync(m->site[q], z, 16, cudaMemcpyHostToDevice, m->stream);
+    }
+  }
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_CUDA, "mps_create: init"); }
+  *out = m;
+  return CTEBD_OK;
+}
+
+extern "C" int mps_destroy(ctebd_mps* m) {
+  if (!m) return CTEBD_ERR_ARG;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  for (auto& kv : m->pending) {
+    Work& w = kv.second;
+    if (w.owned) { cudaFree(w.bufA); cudaFree(w.bufB); cudaFree(w.G); cudaFree(w.V); cudaFree(w.J); cudaFree(w.rho); cudaFree(w.perm); cudaFree(w.res); }
+  }
+  for (void* p : m->site) if (p) cudaFree(p);
+  for (double* p : m->lam) if (p) cudaFree(p);
+  if (m->arena) cudaFree(m->arena);
+  if (m->h_res) cudaFreeHost(m->h_res);
+  m->stage.release();
+  m->prof.release();
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+  return CTEBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched pieces
+// ---------------------------------------------------------------------------
+static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind) {
+  if (probs.empty()) return CTEBD_OK;
+  std::vector<long long> off(probs.size() + 1, 0);
+  double fl = 0, by = 0;
+  for (size_t i = 0; i < probs.size(); i++) {
+    const GemmProb& g = probs[i];
+    off[i + 1] = off[i] + gemm_tiles(g, m->fp64);
+    fl += 8.0 * g.M * g.N * (double)g.K * g.batch;
+    by += ((double)g.M * g.K * (g.sA ? g.batch : 1) + (double)g.K * g.N * (g.sB ? g.batch : 1) +
+           (double)g.M * g.N * g.batch) * m->esz;
+  }
+  const GemmProb* dp;
+  const long long* doff;
+  TRY(m->stage.push(probs.data(), probs.size(), &dp));
+  TRY(m->stage.push(off.data(), off.size(), &doff));
+  ProfScope ps(m->prof, m->stream, kind, fl, by);
+  cudaError_t e = m->fp64 ? launch_gemm<double>(dp, doff, (int)probs.size(), off.back(), m->stream)
+                          : launch_gemm<float>(dp, doff, (int)probs.size(), off.back(), m->stream);
+  CUDA_TRY(e);
+  return CTEBD_OK;
+}
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// sizes of one cluster's work buffers
+static void work_sizes(const ctebd_mps* m, Work& w) {
+  const int k = w.k, q0 = w.q0;
+  size_t big = (size_t)w.chiL * ((size_t)1 << k) * w.chiR;
+  size_t rows = (size_t)w.chiL * 2;
+  for (int j = 1; j < k; j++) {  // merge intermediates
+    big = std::max(big, rows * (size_t)m->chi[q0 + j]);
+    rows *= 2;
+  }
+  // split level shapes: n <= 2 * min(chi_max, bound)
+  const size_t nmax = std::min<size_t>(2 * (size_t)std::max(m->cfg.chi_max, w.chiR), (size_t)1 << 30);
+  const int JB = eig_block(m->fp64);
+  const size_t npad = round_up(nmax, 2 * JB);
+  w.bufElems = big;
+  w.nmax = nmax;
+  w.eigElems = npad * npad;
+  w.jElems = std::max(npad * 2 * JB, ((size_t)1 << k) * ((size_t)1 << k));
+}
+
+static int carve_work(ctebd_mps* m, std::vector<Work>& ws) {
+  size_t total = 0;
+  auto al = [](size_t b) { return round_up(b, 256); };
+  for (auto& w : ws) {
+    work_sizes(m, w);
+    total += 2 * al(w.bufElems * m->esz) + 2 * al(w.eigElems * m->esz) + al(w.jElems * m->esz) +
+             al(w.nmax * 8) + al(w.nmax * 4) + al(64);
+  }
+  if (total > m->arena_cap) {
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (m->arena) CUDA_TRY(cudaFree(m->arena));
+    m->arena = nullptr;
+    m->arena_cap = 0;
+    const size_t want = total + total / 4;
+    if (cudaMalloc(&m->arena, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CTEBD_ERR_OOM, "workspace arena of " + std::to_string(want >> 20) + " MiB");
+    }
+    m->arena_cap = want;
+  }
+  unsigned char* p = (unsigned char*)m->arena;
+  for (auto& w : ws) {
+    w.bufA = p; p += al(w.bufElems * m->esz);
+    w.bufB = p; p += al(w.bufElems * m->esz);
+    w.G = p; p += al(w.eigElems * m->esz);
+    w.V = p; p += al(w.eigElems * m->esz);
+    w.J = p; p += al(w.jElems * m->esz);
+    w.rho = (double*)p; p += al(w.nmax * 8);
+    w.perm = (int*)p; p += al(w.nmax * 4);
+    w.res = (double*)p; p += al(64);
+  }
+  return CTEBD_OK;
+}
+
+static int alloc_owned(ctebd_mps* m, Work& w) {
+  work_sizes(m, w);
+  auto A = [&](void** p, size_t b) -> int {
+    if (cudaMallocAsync(p, std::max<size_t>(b, 16), m->stream) != cudaSuccess) return fail(CTEBD_ERR_OOM, "work buffer");
+    return CTEBD_OK;
+  };
+  TRY(A(&w.bufA, w.bufElems * m->esz));
+  TRY(A(&w.bufB, w.bufElems * m->esz));
+  TRY(A(&w.G, w.eigElems * m->esz));
+  TRY(A(&w.V, w.eigElems * m->esz));
+  TRY(A(&w.J, w.jElems * m->esz));
+  TRY(A((void**)&w.rho, w.nmax * 8));
+  TRY(A((void**)&w.perm, w.nmax * 4));
+  TRY(A((void**)&w.res, 64));
+  w.owned = true;
+  return CTEBD_OK;
+}
+
+static void free_owned(ctebd_mps* m, Work& w) {
+  if (!w.owned) return;
+  for (void* p : {w.bufA, w.bufB, w.G, w.V, w.J, (void*)w.rho, (void*)w.perm, (void*)w.res})
+    if (p) cudaFreeAsync(p, m->stream);
+  w.owned = false;
+}
+
+// merge k sites and apply U: theta' ends in bufA (Sec. III.A exact contraction)
+static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<const double*>& Us) {
+  const int kmax = [&] { int x = 0; for (auto& w : ws) x = std::max(x, w.k); return x; }();
+  std::vector<void*> cur(ws.size()), other(ws.size());
+  for (size_t i = 0; i < ws.size(); i++) { cur[i] = nullptr; }
+  // level j: T_{j} = T_{j-1} * B_{q0+j}; T_0 = site q0
+  for (int j = 1; j < kmax; j++) {
+    std::vector<GemmProb> probs;
+    for (size_t i = 0; i < ws.size(); i++) {
+      Work& w = ws[i];
+      if (j >= w.k) continue;
+      const int rows = w.chiL << j;  // rows of T_{j-1} viewed (chiL 2^j) x chi[q0+j]
+      const int kdim = m->chi[w.q0 + j];
+      const int ncol = 2 * m->chi[w.q0 + j + 1];
+      void* dst = (cur[i] == w.bufA) ? w.bufB : w.bufA;
+      GemmProb p{};
+      p.M = rows; p.N = ncol; p.K = kdim; p.batch = 1;
+      p.A = cur[i] ? cur[i] : m->site[w.q0]; p.lda = kdim; p.opA = 0;
+      p.B = m->site[w.q0 + j]; p.ldb = ncol; p.opB = 0;
+      p.C = dst; p.ldc = ncol; p.alpha = 1.0;
+      probs.push_back(p);
+      cur[i] = dst;
+    }
+    TRY(run_gemms(m, probs, KK_GEMM_MERGE));
+  }
+  // U (host c128) -> device run precision, then theta' = U theta per left index
+  std::vector<GemmProb> probs;
+  for (size_t i = 0; i < ws.size(); i++) {
+    Work& w = ws[i];
+    const long long D = 1LL << w.k;
+    const double* dU;
+    TRY(m->stage.push(Us[i], (size_t)(2 * D * D), &dU));
+    void* src = cur[i] ? cur[i] : m->site[w.q0];
+    // convert U into the spare half of the non-source buffer's tail: use J scratch
+    void* Ud = w.J;
+    if ((size_t)(D * D) > w.jElems) return fail(CTEBD_ERR_ARG, "cluster too large for U scratch");
+    cudaError_t e = m->fp64 ? launch_convert_from_c128<double>(dU, Ud, D * D, m->stream)
+                            : launch_convert_from_c128<float>(dU, Ud, D * D, m->stream);
+    CUDA_TRY(e);
+    void* dst = (src == w.bufA) ? w.bufB : w.bufA;
+    GemmProb p{};
+    p.M = (int)D; p.N = w.chiR; p.K = (int)D; p.batch = w.chiL;
+    p.A = Ud; p.lda = (int)D; p.opA = 0; p.sA = 0;
+    p.B = src; p.ldb = w.chiR; p.opB = 0; p.sB = D * w.chiR;
+    p.C = dst; p.ldc = w.chiR; p.sC = D * w.chiR; p.alpha = 1.0;
+    probs.push_back(p);
+    if (dst != w.bufA) {
+      // keep theta' in bufA: swap the roles of the two buffers for this work item
+      std::swap(w.bufA, w.bufB);
+    }
+  }
+  TRY(run_gemms(m, probs, KK_GEMM_U));
+  for (auto& w : ws) w.rdim = w.chiR;
+  return CTEBD_OK;
+}
+
+// k-1 splits, right to left (Fig. 2 with the truncation of Fig. 3)
+static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::vector<double>>& fs) {
+  const bool f64 = m->fp64;
+  const int JB = eig_block(f64);
+  const double floor_rel = f64 ? 1e-13 : 1e-6;
+  fs.assign(ws.size(), {});
+  int kmax = 0;
+  for (auto& w : ws) kmax = std::max(kmax, w.k);
+  for (int lev = 1; lev < kmax; lev++) {
+    std::vector<int> act;
+    for (size_t i = 0; i < ws.size(); i++) if (ws[i].k - 1 >= lev) act.push_back((int)i);
+    if (act.empty()) break;
+    const int na = (int)act.size();
+    std::vector<int> mm(na), nn(na), npad(na), nbv(na), shift(na);
+    int max_npad = 0, max_nb = 0, max_n = 0, max_m = 0;
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      const int j = w.k - lev;  // bond q0 + j is split off
+      mm[a] = w.chiL << j;
+      nn[a] = 2 * w.rdim;
+      shift[a] = j;
+      npad[a] = (int)round_up(nn[a], 2 * JB);
+      nbv[a] = npad[a] / JB;
+      max_npad = std::max(max_npad, npad[a]);
+      max_nb = std::max(max_nb, nbv[a]);
+      max_n = std::max(max_n, nn[a]);
+      max_m = std::max(max_m, mm[a]);
+      if ((size_t)npad[a] * npad[a] > w.eigElems) return fail(CTEBD_ERR_ARG, "internal: eig buffer");
+      CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)npad[a] * npad[a] * m->esz, m->stream));
+      CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * nn[a], m->stream));
+    }
+    // Gram G = Mbar^H diag(lambda_L^2) Mbar
+    std::vector<GemmProb> probs;
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      GemmProb p{};
+      p.M = nn[a]; p.N = nn[a]; p.K = mm[a]; p.batch = 1;
+      p.A = w.bufA; p.lda = nn[a]; p.opA = 1;
+      p.B = w.bufA; p.ldb = nn[a]; p.opB = 0;
+      p.C = w.G; p.ldc = npad[a];
+      p.kw = m->lam[w.q0];
+      p.kw_shift = shift[a];
+      p.alpha = 1.0;
+      probs.push_back(p);
+    }
+    TRY(run_gemms(m, probs, KK_GEMM_GRAM));
+    // eigen-decomposition of every G
+    std::vector<EigProb> eps(na);
+    double* d_off = nullptr;
+    CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * 2 * na, m->stream));
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      eps[a].G = w.G; eps[a].V = w.V; eps[a].J = w.J;
+      eps[a].npad = npad[a]; eps[a].nb = nbv[a]; eps[a].active = 1;
+      eps[a].off = d_off + 2 * a;
+    }
+    const EigProb* dep;
+    TRY(m->stage.push(eps.data(), eps.size(), &dep));
+    {
+      ProfScope ps(m->prof, m->stream, KK_EIG_INIT, 0, 0);
+      CUDA_TRY(f64 ? launch_eig_init<double>(dep, na, max_npad, m->stream)
+                   : launch_eig_init<float>(dep, na, max_npad, m->stream));
+    }
+    std::vector<double> hoff(2 * na);
+    const int max_sweeps = 30;
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+      CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 2 * na, m->stream));
+      for (int t = 0; t < max_nb - 1; t++) {
+        // algorithmic work of this round over the problems still active
+        double fin = 0, bin = 0, fap = 0, bap = 0;
+        const double D = 2.0 * JB;
+        for (int a = 0; a < na; a++) {
+          if (!eps[a].active || t >= nbv[a] - 1) continue;
+          const double h = nbv[a] / 2, np2 = (double)npad[a] * npad[a];
+          bin += 2 * h * D * D * m->esz;                  // read blocks, write J
+          fap += 24.0 * h * h * D * D * D;                 // J^H G J and V J (2 + 1 complex GEMMs)
+          bap += (4 * np2 + h * D * D) * m->esz;           // G, V read+write, J read
+        }
+        {
+          ProfScope ps(m->prof, m->stream, KK_EIG_INNER, fin, bin);
+          CUDA_TRY(f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
+                       : launch_eig_inner<float>(dep, na, max_nb, t, m->stream));
+        }
+        {
+          ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, fap, bap);
+          CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
+                       : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
+        }
+      }
+      CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, m->stream));
+      CUDA_TRY(cudaStreamSynchronize(m->stream));
+      bool any = false;
+      for (int a = 0; a < na; a++) {
+        if (!eps[a].active) continue;
+        if (hoff[2 * a] == 0.0) eps[a].active = 0; else any = true;
+      }
+      if (!any) break;
+      m->stage.reset();
+      TRY(m->stage.push(eps.data(), eps.size(), &dep));
+    }
+    CUDA_TRY(cudaFreeAsync(d_off, m->stream));
+    // Rfull = Mbar V (bufB), weighted column norms rho
+    probs.clear();
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      GemmProb p{};
+      p.M = mm[a]; p.N = nn[a]; p.K = nn[a]; p.batch = 1;
+      p.A = w.bufA; p.lda = nn[a]; p.opA = 0;
+      p.B = w.V; p.ldb = npad[a]; p.opB = 0;
+      p.C = w.bufB; p.ldc = nn[a]; p.alpha = 1.0;
+      probs.push_back(p);
+    }
+    TRY(run_gemms(m, probs, KK_GEMM_PROJ));
+    {
+      std::vector<const void*> R(na);
+      std::vector<const double*> L(na);
+      std::vector<double*> rho(na);
+      for (int a = 0; a < na; a++) {
+        Work& w = ws[act[a]];
+        R[a] = w.bufB; L[a] = m->lam[w.q0]; rho[a] = w.rho;
+      }
+      const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
+      TRY(m->stage.push(R.data(), na, (const void* const**)&dR));
+      TRY(m->stage.push(mm.data(), na, &dm));
+      TRY(m->stage.push(nn.data(), na, &dn));
+      TRY(m->stage.push(shift.data(), na, &dsh));
+      TRY(m->stage.push(L.data(), na, (const double* const**)&dL));
+      TRY(m->stage.push(rho.data(), na, (double* const**)&drho));
+      double by = 0;
+      for (int a = 0; a < na; a++) by += (double)mm[a] * nn[a] * m->esz;
+      ProfScope ps(m->prof, m->stream, KK_COLNORM, 0, by);
+      CUDA_TRY(f64 ? launch_colnorm_batch<double>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream)
+                   : launch_colnorm_batch<float>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream));
+    }
+    // truncation select: lambda of bond q0+j written in place
+    std::vector<SelProb> sp(na);
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      const int j = w.k - lev;
+      sp[a].rho = w.rho; sp[a].n = nn[a]; sp[a].perm = w.perm;
+      sp[a].lam_out = m->lam[w.q0 + j]; sp[a].res = w.res;
+      if (nn[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
+    }
+    const SelProb* dsp;
+    TRY(m->stage.push(sp.data(), na, &dsp));
+    {
+      ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
+      CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, floor_rel * floor_rel, m->stream));
+    }
+    if ((size_t)na > m->h_res_cap) return fail(CTEBD_ERR_ARG, "too many clusters");
+    for (int a = 0; a < na; a++)
+      CUDA_TRY(cudaMemcpyAsync(m->h_res + 4 * a, ws[act[a]].res, 4 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    m->stage.reset();
+    // write back: new right sites, unweighted remainders
+    std::vector<GatherProb> gp;
+    long long maxe = 0;
+    for (int a = 0; a < na; a++) {
+      Work& w = ws[act[a]];
+      const int j = w.k - lev;
+      const int r = (int)m->h_res[4 * a];
+      const double f = m->h_res[4 * a + 1], W = m->h_res[4 * a + 2], kept = m->h_res[4 * a + 3];
+      if (!(kept > 0) || !std::isfinite(W)) return fail(CTEBD_ERR_NUMERIC, "split: non-finite or zero weight");
+      const int bnd = w.q0 + j;
+      TRY(ensure_site(m, bnd, (size_t)r * nn[a]));
+      GatherProb g0{};
+      g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = nn[a]; g0.r = r; g0.ld = npad[a]; g0.mode = 0;
+      gp.push_back(g0);
+      GatherProb g1{};
+      g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = mm[a]; g1.r = r; g1.ld = nn[a]; g1.mode = 1;
+      g1.scale = 1.0 / std::sqrt(kept);
+      gp.push_back(g1);
+      maxe = std::max(maxe, std::max((long long)r * nn[a], (long long)r * mm[a]));
+      m->chi[bnd] = r;
+      w.rdim = r;
+      m->logF += std::log(f);
+      fs[act[a]].push_back(f);
+      const double row[8] = {(double)w.q0, (double)w.k, (double)bnd, (double)mm[a], (double)nn[a], (double)r, f, W};
+      m->splitlog.insert(m->splitlog.end(), row, row + 8);
+    }
+    const GatherProb* dgp;
+    TRY(m->stage.push(gp.data(), gp.size(), &dgp));
+    double gby = 0;
+    for (auto& g : gp) gby += 2.0 * g.rows * g.r * m->esz;
+    ProfScope psg(m->prof, m->stream, KK_GATHER, 0, gby);
+    CUDA_TRY(f64 ? launch_gather<double>(dgp, (int)gp.size(), maxe, m->stream)
+                 : launch_gather<float>(dgp, (int)gp.size(), maxe, m->stream));
+  }
+  // leftmost site of every cluster: the remainder (chiL*2 x r1)
+  for (auto& w : ws) {
+    const size_t elems = (size_t)w.chiL * 2 * w.rdim;
+    TRY(ensure_site(m, w.q0, elems));
+    CUDA_TRY(cudaMemcpyAsync(m->site[w.q0], w.bufA, elems * m->esz, cudaMemcpyDeviceToDevice, m->stream));
+  }
+  return CTEBD_OK;
+}
+
+static int make_work(ctebd_mps* m, const ctebd_cluster* c, Work& w) {
+  if (!c || c->k < 2 || c->q0 < 0 || c->q0 + c->k > m->n) return fail(CTEBD_ERR_ARG, "cluster out of range (k >= 2 required)");
+  if (c->k > 12) return fail(CTEBD_ERR_ARG, "cluster too large");
+  w.q0 = c->q0; w.k = c->k; w.chiL = m->chi[c->q0]; w.chiR = m->chi[c->q0 + c->k];
+  const long long D = 1LL << c->k;
+  const long long theta = (long long)w.chiL * D * w.chiR;
+  if (theta > (1LL << 31)) return fail(CTEBD_ERR_ARG, "cluster tensor too large");
+  return CTEBD_OK;
+}
+
+extern "C" int step(ctebd_mps* m, const ctebd_cluster* c, int n, const double* const* U, double* f_out) {
+  if (!m || n < 0 || (n > 0 && (!c || !U))) return fail(CTEBD_ERR_ARG, "step: bad args");
+  if (n == 0) return CTEBD_OK;
+  std::vector<Work> ws(n);
+  std::vector<char> used(m->n, 0);
+  for (int i = 0; i < n; i++) {
+    TRY(make_work(m, &c[i], ws[i]));
+    for (int t = 0; t < c[i].k; t++) {
+      if (used[c[i].q0 + t]) return fail(CTEBD_ERR_ARG, "step: clusters overlap");
+      used[c[i].q0 + t] = 1;
+    }
+    if (m->pending.count(c[i].q0)) return fail(CTEBD_ERR_STATE, "step: cluster pending from apply_cluster");
+  }
+  m->splitlog.clear();
+  m->stage.reset();
+  TRY(carve_work(m, ws));
+  std::vector<const double*> Us(U, U + n);
+  TRY(merge_apply(m, ws, Us));
+  std::vector<std::vector<double>> fs;
+  TRY(split_levels(m, ws, fs));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (f_out) {
+    size_t o = 0;
+    for (int i = 0; i < n; i++) for (double f : fs[i]) f_out[o++] = f;
+  }
+  return CTEBD_OK;
+}
+
+extern "C" int apply_cluster(ctebd_mps* m, const ctebd_cluster* c, const double* U) {
+  if (!m || !U) return fail(CTEBD_ERR_ARG, "apply_cluster: null argument");
+  Work w;
+  TRY(make_work(m, c, w));
+  if (m->pending.count(c->q0)) return fail(CTEBD_ERR_STATE, "apply_cluster: cluster already pending");
+  m->stage.reset();
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  TRY(alloc_owned(m, w));
+  std::vector<Work> ws{w};
+  std::vector<const double*> Us{U};
+  int rc = merge_apply(m, ws, Us);
+  if (rc) { free_owned(m, ws[0]); return rc; }
+  m->pending[c->q0] = ws[0];
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int truncate_split(ctebd_mps* m, const ctebd_cluster* c, double* f_out) {
+  if (!m || !c) return fail(CTEBD_ERR_ARG, "truncate_split: null argument");
+  auto it = m->pending.find(c->q0);
+  if (it == m->pending.end() || it->second.k != c->k) return fail(CTEBD_ERR_STATE, "truncate_split: no pending apply_cluster for this cluster");
+  std::vector<Work> ws{it->second};
+  m->pending.erase(it);
+  m->splitlog.clear();
+  m->stage.reset();
+  std::vector<std::vector<double>> fs;
+  int rc = split_levels(m, ws, fs);
+  free_owned(m, ws[0]);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (f_out) for (size_t i = 0; i < fs[0].size(); i++) f_out[i] = fs[0][i];
+  return CTEBD_OK;
+}
+
+extern "C" int apply_1q(ctebd_mps* m, int q, const double* u) {
+  if (!m || !u || q < 0 || q >= m->n) return fail(CTEBD_ERR_ARG, "apply_1q: bad args");
+  m->stage.reset();
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  void* s = m->site[q];
+  const int cl = m->chi[q], cr = m->chi[q + 1];
+  void* const* ds; const int *dcl, *dcr; const double* du;
+  TRY(m->stage.push(&s, 1, (void* const**)&ds));
+  TRY(m->stage.push(&cl, 1, &dcl));
+  TRY(m->stage.push(&cr, 1, &dcr));
+  TRY(m->stage.push(u, 8, &du));
+  {
+    ProfScope ps(m->prof, m->stream, KK_ONEQ, 28.0 * cl * cr, 4.0 * cl * cr * m->esz);
+    CUDA_TRY(m->fp64 ? launch_apply_1q<double>(ds, dcl, dcr, du, 1, (long long)cl * cr, m->stream)
+                     : launch_apply_1q<float>(ds, dcl, dcr, du, 1, (long long)cl * cr, m->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int apply_singletons(ctebd_mps* m, const ctebd_gate* gates, int n_gates,
+                                const ctebd_cluster* cl, int ncl, int lo, int hi) {
+  if (!m || n_gates < 0 || (n_gates && !gates) || ncl < 0 || (ncl && !cl))
+    return fail(CTEBD_ERR_ARG, "apply_singletons: bad args");
+  std::vector<char> inc(m->n, 0);
+  for (int c = 0; c < ncl; c++)
+    for (int t = 0; t < cl[c].k; t++) {
+      const int q = cl[c].q0 + t;
+      if (q < 0 || q >= m->n) return fail(CTEBD_ERR_ARG, "apply_singletons: cluster out of range");
+      inc[q] = 1;
+    }
+  std::vector<int> order;
+  for (int i = 0; i < n_gates; i++)
+    if (gates[i].layer > lo && gates[i].layer <= hi && gates[i].n_q == 1 && !inc[gates[i].q[0]]) order.push_back(i);
+  if (order.empty()) return CTEBD_OK;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+  std::map<int, std::vector<cd>> prod;
+  for (int gi : order) {
+    const ctebd_gate& g = gates[gi];
+    if (g.q[0] < 0 || g.q[0] >= m->n) return fail(CTEBD_ERR_ARG, "apply_singletons: qubit out of range");
+    cd u[16];
+    if (gate_dim(g.kind, g.param, u) != 2) return fail(CTEBD_ERR_ARG, "apply_singletons: not a one-qubit gate");
+    auto it = prod.find(g.q[0]);
+    if (it == prod.end()) { prod[g.q[0]] = std::vector<cd>(u, u + 4); continue; }
+    std::vector<cd>& p = it->second;
+    const cd r0 = u[0] * p[0] + u[1] * p[2], r1 = u[0] * p[1] + u[1] * p[3];
+    const cd r2 = u[2] * p[0] + u[3] * p[2], r3 = u[2] * p[1] + u[3] * p[3];
+    p = {r0, r1, r2, r3};
+  }
+  std::vector<void*> sites;
+  std::vector<int> cls, crs;
+  std::vector<double> us;
+  long long maxe = 0;
+  for (auto& kv : prod) {
+    const int q = kv.first;
+    sites.push_back(m->site[q]);
+    cls.push_back(m->chi[q]);
+    crs.push_back(m->chi[q + 1]);
+    for (const cd& z : kv.second) { us.push_back(z.real()); us.push_back(z.imag()); }
+    maxe = std::max(maxe, (long long)m->chi[q] * m->chi[q + 1]);
+  }
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->stage.reset();
+  void* const* ds; const int *dcl, *dcr; const double* du;
+  TRY(m->stage.push(sites.data(), sites.size(), (void* const**)&ds));
+  TRY(m->stage.push(cls.data(), cls.size(), &dcl));
+  TRY(m->stage.push(crs.data(), crs.size(), &dcr));
+  TRY(m->stage.push(us.data(), us.size(), &du));
+  double e1 = 0;
+  for (size_t i = 0; i < sites.size(); i++) e1 += (double)cls[i] * crs[i];
+  {
+    ProfScope ps(m->prof, m->stream, KK_ONEQ, 28.0 * e1, 4.0 * e1 * m->esz);
+    CUDA_TRY(m->fp64 ? launch_apply_1q<double>(ds, dcl, dcr, du, (int)sites.size(), maxe, m->stream)
+                     : launch_apply_1q<float>(ds, dcl, dcr, du, (int)sites.size(), maxe, m->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int fidelity(const ctebd_mps* m, double* F) {
+  if (!m || !F) return fail(CTEBD_ERR_ARG, "fidelity: null argument");
+  *F = std::exp(m->logF);
+  return CTEBD_OK;
+}
+
+extern "C" int amplitude(const ctebd_mps* mc, const uint8_t* bits, double* re, double* im) {
+  ctebd_mps* m = const_cast<ctebd_mps*>(mc);
+  if (!m || !bits || !re || !im) return fail(CTEBD_ERR_ARG, "amplitude: null argument");
+  int cmax = 1;
+  for (int c : m->chi) cmax = std::max(cmax, c);
+  double2 *va = nullptr, *vb = nullptr;
+  CUDA_TRY(cudaMallocAsync(&va, sizeof(double2) * cmax, m->stream));
+  CUDA_TRY(cudaMallocAsync(&vb, sizeof(double2) * cmax, m->stream));
+  const double one[2] = {1.0, 0.0};
+  CUDA_TRY(cudaMemcpyAsync(va, one, sizeof(one), cudaMemcpyHostToDevice, m->stream));
+  for (int q = 0; q < m->n; q++) {
+    if (bits[q] > 1) return fail(CTEBD_ERR_ARG, "amplitude: bits must be 0/1");
+    ProfScope ps(m->prof, m->stream, KK_AMP, 8.0 * m->chi[q] * m->chi[q + 1], (double)m->chi[q] * m->chi[q + 1] * m->esz);
+    CUDA_TRY(m->fp64 ? launch_amp_step<double>(va, vb, m->site[q], m->chi[q], m->chi[q + 1], bits[q], m->stream)
+                     : launch_amp_step<float>(va, vb, m->site[q], m->chi[q], m->chi[q + 1], bits[q], m->stream));
+    std::swap(va, vb);
+  }
+  double out[2];
+  CUDA_TRY(cudaMemcpyAsync(out, va, sizeof(out), cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaFreeAsync(va, m->stream));
+  CUDA_TRY(cudaFreeAsync(vb, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  *re = out[0];
+  *im = out[1];
+  return CTEBD_OK;
+}
+
+extern "C" int mps_bond_dims(const ctebd_mps* m, int* chi) {
+  if (!m || !chi) return fail(CTEBD_ERR_ARG, "mps_bond_dims: null argument");
+  std::memcpy(chi, m->chi.data(), sizeof(int) * m->chi.size());
+  return CTEBD_OK;
+}
+
+extern "C" int mps_to_host(const ctebd_mps* mc, int q, double* buf, size_t cap) {
+  ctebd_mps* m = const_cast<ctebd_mps*>(mc);
+  if (!m || !buf || q < 0 || q >= m->n) return fail(CTEBD_ERR_ARG, "mps_to_host: bad args");
+  const long long n = (long long)m->chi[q] * 2 * m->chi[q + 1];
+  if ((size_t)(2 * n) > cap) return fail(CTEBD_ERR_ARG, "mps_to_host: buffer too small");
+  double* d = nullptr;
+  CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * 2 * n, m->stream));
+  CUDA_TRY(m->fp64 ? launch_convert_to_c128<double>(m->site[q], d, n, m->stream)
+                   : launch_convert_to_c128<float>(m->site[q], d, n, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(buf, d, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaFreeAsync(d, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int mps_lambda_to_host(const ctebd_mps* mc, int b, double* buf, size_t cap) {
+  ctebd_mps* m = const_cast<ctebd_mps*>(mc);
+  if (!m || !buf || b < 0 || b > m->n) return fail(CTEBD_ERR_ARG, "mps_lambda_to_host: bad args");
+  if ((size_t)m->chi[b] > cap) return fail(CTEBD_ERR_ARG, "mps_lambda_to_host: buffer too small");
+  CUDA_TRY(cudaMemcpyAsync(buf, m->lam[b], sizeof(double) * m->chi[b], cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+static int check_chi(const ctebd_mps* m, const int* chi) {
+  if (chi[0] != 1 || chi[m->n] != 1) return fail(CTEBD_ERR_ARG, "mps_load: boundary bonds must be 1");
+  for (int b = 0; b <= m->n; b++)
+    if (chi[b] < 1 || chi[b] > m->lam_cap) return fail(CTEBD_ERR_ARG, "mps_load: chi out of range");
+  return CTEBD_OK;
+}
+
+extern "C" int mps_load(ctebd_mps* m, const int* chi, const double* const* sites, const double* const* lams) {
+  if (!m || !chi || !sites || !lams) return fail(CTEBD_ERR_ARG, "mps_load: null argument");
+  TRY(check_chi(m, chi));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  for (int q = 0; q < m->n; q++) {
+    const long long n = (long long)chi[q] * 2 * chi[q + 1];
+    TRY(ensure_site(m, q, (size_t)n));
+    double* d = nullptr;
+    CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * 2 * n, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(d, sites[q], sizeof(double) * 2 * n, cudaMemcpyHostToDevice, m->stream));
+    CUDA_TRY(m->fp64 ? launch_convert_from_c128<double>(d, m->site[q], n, m->stream)
+                     : launch_convert_from_c128<float>(d, m->site[q], n, m->stream));
+    CUDA_TRY(cudaFreeAsync(d, m->stream));
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+  }
+  for (int b = 0; b <= m->n; b++)
+    CUDA_TRY(cudaMemcpyAsync(m->lam[b], lams[b], sizeof(double) * chi[b], cudaMemcpyHostToDevice, m->stream));
+  m->chi.assign(chi, chi + m->n + 1);
+  m->logF = 0;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int mps_load_device(ctebd_mps* m, const int* chi, const void* const* sites, const double* const* lams) {
+  if (!m || !chi || !sites || !lams) return fail(CTEBD_ERR_ARG, "mps_load_device: null argument");
+  TRY(check_chi(m, chi));
+  for (int q = 0; q < m->n; q++) {
+    const size_t n = (size_t)chi[q] * 2 * chi[q + 1];
+    TRY(ensure_site(m, q, n));
+    CUDA_TRY(cudaMemcpyAsync(m->site[q], sites[q], n * m->esz, cudaMemcpyDeviceToDevice, m->stream));
+  }
+  for (int b = 0; b <= m->n; b++)
+    CUDA_TRY(cudaMemcpyAsync(m->lam[b], lams[b], sizeof(double) * chi[b], cudaMemcpyDefault, m->stream));
+  m->chi.assign(chi, chi + m->n + 1);
+  m->logF = 0;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int mps_split_log(const ctebd_mps* m, double* rows, int cap, int* n_rows) {
+  if (!m || !n_rows) return fail(CTEBD_ERR_ARG, "mps_split_log: null argument");
+  const int nr = (int)(m->splitlog.size() / 8);
+  *n_rows = nr;
+  if (rows) std::memcpy(rows, m->splitlog.data(), sizeof(double) * 8 * std::min(nr, cap));
+  return CTEBD_OK;
+}
+
+extern "C" int ctebd_profile(ctebd_mps* m, int mode) {
+  if (!m) return fail(CTEBD_ERR_ARG, "ctebd_profile: null");
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->prof.drain();
+  m->prof.reset();
+  m->prof.on = mode != 0;
+  return CTEBD_OK;
+}
+
+extern "C" int ctebd_profile_read(ctebd_mps* m, double* rows, int cap, int* n_kinds) {
+  if (!m || !n_kinds) return fail(CTEBD_ERR_ARG, "ctebd_profile_read: null");
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->prof.drain();
+  *n_kinds = KK_COUNT;
+  for (int k = 0; k < KK_COUNT && k < cap && rows; k++) {
+    rows[4 * k + 0] = m->prof.launches[k];
+    rows[4 * k + 1] = m->prof.ms[k];
+    rows[4 * k + 2] = m->prof.flops[k];
+    rows[4 * k + 3] = m->prof.bytes[k];
+  }
+  return CTEBD_OK;
+}
+
+extern "C" int ctebd_kernel_name(int kind, char* buf, size_t n) {
+  if (kind < 0 || kind >= KK_COUNT || !buf || !n) return fail(CTEBD_ERR_ARG, "ctebd_kernel_name: bad kind");
+  std::snprintf(buf, n, "%s", kKindNames[kind]);
+  return CTEBD_OK;
+}

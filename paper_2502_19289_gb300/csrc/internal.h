@@ -1,0 +1,99 @@
+// internal.h -- declarations shared by the host orchestration (host.cpp) and
+// the CUDA kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace ctebd {
+
+// One complex GEMM of a grouped launch, interleaved complex of real type R:
+//   C[b] (M x N) = alpha * op(A[b]) (M x K) * op(B[b]) (K x N)
+// op = 0: X[r][c] = X[r*ld + c];  op = 1: X[r][c] = conj(X[c*ld + r]).
+// kw (optional): real weights; column k of op(A) is multiplied by
+// kw[k >> kw_shift]^2 (the Schmidt-weighted Gram matrix M^H diag(lambda^2) M).
+struct GemmProb {
+  int M, N, K, batch;
+  long long sA, sB, sC;  // batch strides in complex elements
+  const void* A;
+  const void* B;
+  void* C;
+  int lda, ldb, ldc;
+  int opA, opB;
+  const double* kw;
+  int kw_shift;
+  double alpha;
+};
+
+// One Hermitian eigenproblem of the batched block-Jacobi solver.  G and V are
+// row-major npad x npad (npad = nb * JB), G Hermitian (zero padded), V
+// accumulates the rotations (starts as identity).  J holds nb/2 unitary
+// blocks of (2 JB)^2 for the current round.
+struct EigProb {
+  void* G;
+  void* V;
+  void* J;
+  int npad;
+  int nb;       // number of JB-blocks, even
+  int active;   // 0: converged, skip
+  double* off;  // [0] off-diagonal Frobenius^2, [1] total Frobenius^2
+};
+
+// Per-problem truncation inputs/outputs of one split level.
+struct SelProb {
+  const double* rho;   // n weighted column norms
+  int n;
+  int* perm;           // out: kept column indices, descending rho
+  double* lam_out;     // out: renormalised kept spectrum (fp64)
+  double* res;         // out: [0] r, [1] f, [2] W, [3] kept
+};
+
+struct GatherProb {
+  const void* src;     // V (ld) or Rfull (ld)
+  void* dst;
+  const int* perm;
+  int rows, r, ld;
+  int mode;            // 0: site = conj(V[c][perm[mu]]) -> dst[mu][c] (rows = n)
+                       // 1: rem  = Rfull[row][perm[mu]] * scale -> dst[row][mu]
+  double scale;
+};
+
+// Launchers (R = float or double).  Descriptor arrays are device pointers.
+template <typename R>
+cudaError_t launch_gemm(const GemmProb* d_probs, const long long* d_tile_off, int n_probs,
+                        long long total_tiles, cudaStream_t s);
+// tile bookkeeping helper (host): tiles of a problem in the GEMM grid
+long long gemm_tiles(const GemmProb& p, bool fp64);
+
+template <typename R>
+cudaError_t launch_eig_init(const EigProb* d_probs, int n_probs, int max_npad, cudaStream_t s);
+template <typename R>
+cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, int round,
+                             cudaStream_t s);
+template <typename R>
+cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round,
+                             cudaStream_t s);
+int eig_block(bool fp64);  // JB
+
+template <typename R>
+cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n,
+                                 const double* const* d_lam, const int* d_shift,
+                                 double* const* d_rho, int n_probs, int max_n, int max_m,
+                                 cudaStream_t s);
+cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff,
+                          double floor2, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gather(const GatherProb* d_probs, int n_probs, long long max_elems,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t launch_apply_1q(void* const* d_sites, const int* d_cl, const int* d_cr,
+                            const double* d_u, int n_sites, long long max_elems, cudaStream_t s);
+template <typename R>
+cudaError_t launch_amp_step(const void* v_in, void* v_out, const void* site, int cl, int cr,
+                            int bit, cudaStream_t s);
+template <typename R>
+cudaError_t launch_convert_from_c128(const double* src, void* dst, long long n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_convert_to_c128(const void* src, double* dst, long long n, cudaStream_t s);
+
+}  // namespace ctebd

@@ -1,0 +1,694 @@
+// kernels.cu -- CUDA kernels of the cluster update (sm_103a).
+//
+// The split of Fig. 2 / Fig. 3 is computed from the Schmidt-weighted Gram
+// matrix G = M^H diag(lambda_L^2) M (grouped GEMM), its eigenvectors V from a
+// batched block-Jacobi solver, and the weighted column norms of Mbar V, which
+// give the kept weights directly from M (Eq. 4 numerator and denominator).
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace ctebd {
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename T> __device__ __forceinline__ T cmk(double re, double im);
+template <> __device__ __forceinline__ float2 cmk<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ double2 cmk<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  T r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+template <typename T> __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename T> __device__ __forceinline__ T cscale(T a, double s) {
+  a.x = (decltype(a.x))(a.x * s); a.y = (decltype(a.y))(a.y * s); return a;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped complex GEMM, 64x64 output tile, 256 threads (4x4 per thread).
+// Merge chain (theta), U application, Gram matrix and Mbar*V all use it.
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs,
+                                              const long long* __restrict__ tile_off, int n_probs) {
+  using CT = typename C2<R>::T;
+  __shared__ CT As[GBK][GBM + 1];
+  __shared__ CT Bs[GBK][GBN + 1];
+  const long long tid_tile = blockIdx.x;
+  int lo = 0, hi = n_probs;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (tile_off[mid] <= tid_tile) lo = mid; else hi = mid;
+  }
+  const GemmProb P = probs[lo];
+  long long t = tid_tile - tile_off[lo];
+  const int tilesN = (P.N + GBN - 1) / GBN, tilesM = (P.M + GBM - 1) / GBM;
+  const int tn = (int)(t % tilesN);
+  t /= tilesN;
+  const int tm = (int)(t % tilesM);
+  const long long bidx = t / tilesM;
+  const CT* A = (const CT*)P.A + bidx * P.sA;
+  const CT* B = (const CT*)P.B + bidx * P.sB;
+  CT* Cm = (CT*)P.C + bidx * P.sC;
+  const int m0 = tm * GBM, n0 = tn * GBN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  CT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = cmk<CT>(0, 0);
+  for (int k0 = 0; k0 < P.K; k0 += GBK) {
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+      const int e = threadIdx.x + it * 256;
+      int m, kk;
+      CT v = cmk<CT>(0, 0);
+      if (P.opA == 0) {
+        m = e / GBK; kk = e % GBK;
+        if (m0 + m < P.M && k0 + kk < P.K) v = A[(long long)(m0 + m) * P.lda + k0 + kk];
+      } else {
+        kk = e / GBM; m = e % GBM;
+        if (m0 + m < P.M && k0 + kk < P.K) v = cconj(A[(long long)(k0 + kk) * P.lda + m0 + m]);
+      }
+      if (P.kw && k0 + kk < P.K) {
+        const double wk = P.kw[(k0 + kk) >> P.kw_shift];
+        v = cscale(v, wk * wk);
+      }
+      As[kk][m] = v;
+      int n;
+      CT w = cmk<CT>(0, 0);
+      if (P.opB == 0) {
+        kk = e / GBN; n = e % GBN;
+        if (n0 + n < P.N && k0 + kk < P.K) w = B[(long long)(k0 + kk) * P.ldb + n0 + n];
+      } else {
+        n = e / GBK; kk = e % GBK;
+        if (n0 + n < P.N && k0 + kk < P.K) w = cconj(B[(long long)(n0 + n) * P.ldb + k0 + kk]);
+      }
+      Bs[kk][n] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk++) {
+      CT a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int n = n0 + tx + 16 * j;
+      if (n < P.N) Cm[(long long)m * P.ldc + n] = cscale(acc[i][j], P.alpha);
+    }
+  }
+}
+
+long long gemm_tiles(const GemmProb& p, bool) {
+  return (long long)((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN) * p.batch;
+}
+
+template <typename R>
+cudaError_t launch_gemm(const GemmProb* d_probs, const long long* d_tile_off, int n_probs,
+                        long long total_tiles, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_gemm<R><<<(unsigned)total_tiles, 256, 0, s>>>(d_probs, d_tile_off, n_probs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm<float>(const GemmProb*, const long long*, int, long long, cudaStream_t);
+template cudaError_t launch_gemm<double>(const GemmProb*, const long long*, int, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Batched block-Jacobi eigensolver for Hermitian G (two-sided, parallel
+// round-robin ordering of JB-blocks).  Per round: (1) every block pair's
+// 2JB x 2JB sub-matrix is diagonalised in shared memory by cyclic Jacobi,
+// giving a unitary J_p; (2) G <- J^H G J and V <- V J tile by tile.
+// ---------------------------------------------------------------------------
+template <typename R> struct EigCfg;
+template <> struct EigCfg<float> { static constexpr int JB = 32; static constexpr int MAXS = 6; };
+template <> struct EigCfg<double> { static constexpr int JB = 16; static constexpr int MAXS = 8; };
+int eig_block(bool fp64) { return fp64 ? EigCfg<double>::JB : EigCfg<float>::JB; }
+
+// Round-robin (circle method) schedule: N players, round t in [0, N-1), slot i.
+__device__ __forceinline__ void circle(int t, int i, int N, int& a, int& b) {
+  const int M = N - 1;
+  if (i == 0) { a = t; b = N - 1; }
+  else { a = (t + i) % M; b = (t - i + M) % M; }
+  if (a > b) { int x = a; a = b; b = x; }
+}
+
+template <typename R>
+__device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R dmax, R& c, R& s,
+                                            typename C2<R>::T& ph, bool& skip) {
+  using CT = typename C2<R>::T;
+  const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+  const R ag = sqrt(g.x * g.x + g.y * g.y);
+  skip = !(ag > (R)4 * eps * sqrt(fabs(a * d))) || !(ag > eps * dmax) || ag == (R)0;
+  if (skip) { c = 1; s = 0; ph = cmk<CT>(1, 0); return; }
+  const R zeta = (d - a) / ((R)2 * ag);
+  R t;
+  if (fabs(zeta) > (R)1e15) t = (R)0.5 / zeta;
+  else t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+  c = (R)1 / sqrt((R)1 + t * t);
+  s = c * t;
+  ph.x = g.x / ag;
+  ph.y = -g.y / ag;  // e^{-i phi}
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ probs, int round) {
+  using CT = typename C2<R>::T;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
+  const EigProb P = probs[blockIdx.y];
+  if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2) return;
+  extern __shared__ unsigned char smraw[];
+  CT* A = reinterpret_cast<CT*>(smraw);
+  CT* Q = A + D * LD;
+  R* cs = reinterpret_cast<R*>(Q + D * LD);
+  R* sn = cs + JB;
+  CT* ph = reinterpret_cast<CT*>(sn + JB);
+  int* pp = reinterpret_cast<int*>(ph + JB);
+  int* pq = pp + JB;
+  __shared__ int nrot;
+  __shared__ R dmax_s;
+  int I, J;
+  circle(round, blockIdx.x, P.nb, I, J);
+  const CT* G = (const CT*)P.G;
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+    const int li = e / D, lj = e % D;
+    const long long gi = li < JB ? (long long)I * JB + li : (long long)J * JB + li - JB;
+    const long long gj = lj < JB ? (long long)I * JB + lj : (long long)J * JB + lj - JB;
+    A[li * LD + lj] = G[gi * P.npad + gj];
+    Q[li * LD + lj] = cmk<CT>(li == lj ? 1 : 0, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R m = 0;
+    for (int i = 0; i < D; i++) m = fmax(m, fabs(A[i * LD + i].x));
+    dmax_s = m;
+  }
+  __syncthreads();
+  int total = 0;
+  for (int sweep = 0; sweep < EigCfg<R>::MAXS; sweep++) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int r = 0; r < D - 1; r++) {
+      if (threadIdx.x < JB) {
+        int p, q;
+        circle(r, threadIdx.x, D, p, q);
+        pp[threadIdx.x] = p; pq[threadIdx.x] = q;
+        R c, s; CT e; bool skip;
+        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], dmax_s, c, s, e, skip);
+        cs[threadIdx.x] = c; sn[threadIdx.x] = s; ph[threadIdx.x] = e;
+        if (!skip) atomicAdd(&nrot, 1);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of A and Q
+        const int row = e / JB, k = e % JB;
+        const int p = pp[k], q = pq[k];
+        const R c = cs[k], s = sn[k];
+        const CT f = ph[k];
+        CT x = A[row * LD + p], y = cmul(A[row * LD + q], f);
+        A[row * LD + p] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
+        A[row * LD + q] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+        x = Q[row * LD + p]; y = cmul(Q[row * LD + q], f);
+        Q[row * LD + p] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
+        Q[row * LD + q] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // rows of A
+        const int col = e / JB, k = e % JB;
+        const int p = pp[k], q = pq[k];
+        const R c = cs[k], s = sn[k];
+        const CT f = cconj(ph[k]);
+        CT x = A[p * LD + col], y = cmul(A[q * LD + col], f);
+        A[p * LD + col] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
+        A[q * LD + col] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+      }
+      __syncthreads();
+    }
+    const int nr = nrot;
+    total += nr;
+    __syncthreads();
+    if (nr == 0) break;
+  }
+  CT* Jo = (CT*)P.J + (long long)blockIdx.x * D * D;
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) Jo[e] = Q[(e / D) * LD + (e % D)];
+  if (threadIdx.x == 0 && total > 0) atomicAdd(P.off, (double)total);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ probs, int round) {
+  using CT = typename C2<R>::T;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, PER = D / 16;
+  const EigProb P = probs[blockIdx.y];
+  if (!P.active || round >= P.nb - 1) return;
+  const int h = P.nb / 2, nG = h * h;
+  const int tile = blockIdx.x;
+  if (tile >= 2 * nG) return;
+  extern __shared__ unsigned char smraw[];
+  CT* S0 = reinterpret_cast<CT*>(smraw);
+  CT* S1 = S0 + D * LD;
+  const bool isG = tile < nG;
+  const int Pp = isG ? tile / h : (tile - nG) / h;
+  const int Qp = isG ? tile % h : (tile - nG) % h;
+  int K1, K2, I1 = 0, I2 = 0;
+  circle(round, Qp, P.nb, K1, K2);
+  if (isG) circle(round, Pp, P.nb, I1, I2);
+  CT* X = (CT*)(isG ? P.G : P.V);
+  const CT* Jb = (const CT*)P.J;
+  auto grow = [&](int li) -> long long {
+    if (!isG) return (long long)Pp * D + li;
+    return li < JB ? (long long)I1 * JB + li : (long long)I2 * JB + li - JB;
+  };
+  auto gcol = [&](int lj) -> long long {
+    return lj < JB ? (long long)K1 * JB + lj : (long long)K2 * JB + lj - JB;
+  };
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+    const int li = e / D, lj = e % D;
+    S0[li * LD + lj] = X[grow(li) * P.npad + gcol(lj)];
+    S1[li * LD + lj] = Jb[(long long)Qp * D * D + e];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  CT acc[PER][PER];
+#pragma unroll
+  for (int i = 0; i < PER; i++)
+#pragma unroll
+    for (int j = 0; j < PER; j++) acc[i][j] = cmk<CT>(0, 0);
+  for (int k = 0; k < D; k++) {          // T = X_tile * J_Q
+    CT a[PER], b[PER];
+#pragma unroll
+    for (int i = 0; i < PER; i++) a[i] = S0[(ty + 16 * i) * LD + k];
+#pragma unroll
+    for (int j = 0; j < PER; j++) b[j] = S1[k * LD + tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < PER; i++)
+#pragma unroll
+      for (int j = 0; j < PER; j++) cfma(acc[i][j], a[i], b[j]);
+  }
+  if (!isG) {
+#pragma unroll
+    for (int i = 0; i < PER; i++)
+#pragma unroll
+      for (int j = 0; j < PER; j++)
+        X[grow(ty + 16 * i) * P.npad + gcol(tx + 16 * j)] = acc[i][j];
+    return;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; i++)
+#pragma unroll
+    for (int j = 0; j < PER; j++) S0[(ty + 16 * i) * LD + tx + 16 * j] = acc[i][j];
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x)
+    S1[(e / D) * LD + (e % D)] = Jb[(long long)Pp * D * D + e];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; i++)
+#pragma unroll
+    for (int j = 0; j < PER; j++) acc[i][j] = cmk<CT>(0, 0);
+  for (int k = 0; k < D; k++) {          // Y = J_P^H * T
+    CT a[PER], b[PER];
+#pragma unroll
+    for (int i = 0; i < PER; i++) a[i] = cconj(S1[k * LD + ty + 16 * i]);
+#pragma unroll
+    for (int j = 0; j < PER; j++) b[j] = S0[k * LD + tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < PER; i++)
+#pragma unroll
+      for (int j = 0; j < PER; j++) cfma(acc[i][j], a[i], b[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < PER; i++)
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+      X[grow(ty + 16 * i) * P.npad + gcol(tx + 16 * j)] = acc[i][j];
+}
+
+template <typename R>
+__global__ void k_eig_init(const EigProb* __restrict__ probs, int max_npad) {
+  using CT = typename C2<R>::T;
+  const EigProb P = probs[blockIdx.y];
+  const long long n2 = (long long)P.npad * P.npad;
+  CT* V = (CT*)P.V;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / P.npad, j = e % P.npad;
+    V[e] = cmk<CT>(i == j ? 1 : 0, 0);
+  }
+}
+
+template <typename R>
+cudaError_t launch_eig_init(const EigProb* d_probs, int n_probs, int max_npad, cudaStream_t s) {
+  if (n_probs <= 0) return cudaSuccess;
+  long long n2 = (long long)max_npad * max_npad;
+  unsigned gx = (unsigned)((n2 + 255) / 256);
+  if (gx > 4096) gx = 4096;
+  k_eig_init<R><<<dim3(gx, n_probs), 256, 0, s>>>(d_probs, max_npad);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static void eig_attrs() {
+  using CT = typename C2<R>::T;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
+  static bool attr = false;
+  if (attr) return;
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int));
+  const size_t sm_apply = 2 * sizeof(CT) * D * LD;
+  cudaFuncSetAttribute(k_eig_inner<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
+  cudaFuncSetAttribute(k_eig_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+  attr = true;
+}
+
+template <typename R>
+cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, int round, cudaStream_t s) {
+  using CT = typename C2<R>::T;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
+  eig_attrs<R>();
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int));
+  k_eig_inner<R><<<dim3(max_nb / 2, n_probs), 256, sm_inner, s>>>(d_probs, round);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round, cudaStream_t s) {
+  using CT = typename C2<R>::T;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
+  eig_attrs<R>();
+  const size_t sm_apply = 2 * sizeof(CT) * D * LD;
+  const int h = max_nb / 2;
+  k_eig_apply<R><<<dim3(2 * h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_eig_init<float>(const EigProb*, int, int, cudaStream_t);
+template cudaError_t launch_eig_init<double>(const EigProb*, int, int, cudaStream_t);
+template cudaError_t launch_eig_inner<float>(const EigProb*, int, int, int, cudaStream_t);
+template cudaError_t launch_eig_inner<double>(const EigProb*, int, int, int, cudaStream_t);
+template cudaError_t launch_eig_apply<float>(const EigProb*, int, int, int, cudaStream_t);
+template cudaError_t launch_eig_apply<double>(const EigProb*, int, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Weighted column norms rho_i = sum_row lambda_L[row >> shift]^2 |R[row][i]|^2
+// in FP64: the Schmidt weight carried by direction i (Eq. 4 terms).
+// ---------------------------------------------------------------------------
+constexpr int CN_ROWS = 256;
+
+template <typename R>
+__global__ void k_colnorm(const void* const* __restrict__ Rs, const int* __restrict__ ms,
+                          const int* __restrict__ ns, const double* const* __restrict__ lams,
+                          const int* __restrict__ shifts, double* const* __restrict__ rhos) {
+  using CT = typename C2<R>::T;
+  const int p = blockIdx.z;
+  const int n = ns[p], m = ms[p];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * CN_ROWS;
+  if (c >= n || r0 >= m) return;
+  const CT* Rm = (const CT*)Rs[p];
+  const double* lam = lams[p];
+  const int sh = shifts[p];
+  const int r1 = min(m, r0 + CN_ROWS);
+  double acc = 0;
+  for (int r = r0; r < r1; r++) {
+    const CT v = Rm[(long long)r * n + c];
+    const double w = lam[r >> sh];
+    acc += w * w * ((double)v.x * v.x + (double)v.y * v.y);
+  }
+  atomicAdd(&rhos[p][c], acc);
+}
+
+template <typename R>
+cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n,
+                                 const double* const* d_lam, const int* d_shift,
+                                 double* const* d_rho, int n_probs, int max_n, int max_m,
+                                 cudaStream_t s) {
+  if (n_probs <= 0) return cudaSuccess;
+  dim3 grid((max_n + 127) / 128, (max_m + CN_ROWS - 1) / CN_ROWS, n_probs);
+  k_colnorm<R><<<grid, 128, 0, s>>>(d_R, d_m, d_n, d_lam, d_shift, d_rho);
+  return cudaGetLastError();
+}
+template cudaError_t launch_colnorm_batch<float>(const void* const*, const int*, const int*,
+                                                 const double* const*, const int*,
+                                                 double* const*, int, int, int, cudaStream_t);
+template cudaError_t launch_colnorm_batch<double>(const void* const*, const int*, const int*,
+                                                  const double* const*, const int*,
+                                                  double* const*, int, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Truncation (Sec. II.B): sort the weights descending, keep the smallest r
+// whose discarded weight is <= cutoff * total, drop numerical zeros
+// (rho <= floor2 * rho_max), cap at chi_max; f = kept / total (Eq. 4); the
+// kept spectrum is renormalised to unit weight.
+// ---------------------------------------------------------------------------
+constexpr int SEL_MAX = 4096;
+
+__global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ probs, int chi_max,
+                                                 double cutoff, double floor2) {
+  extern __shared__ unsigned char smraw[];
+  double* key = reinterpret_cast<double*>(smraw);
+  int* idx = reinterpret_cast<int*>(key + SEL_MAX);
+  __shared__ int r_s;
+  __shared__ double kept_s;
+  const SelProb P = probs[blockIdx.x];
+  const int n = P.n;
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+    key[i] = i < n ? P.rho[i] : -1.0;
+    idx[i] = i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          // "before" = larger key, ties by smaller index
+          const bool i_before_l = key[i] > key[l] || (key[i] == key[l] && idx[i] < idx[l]);
+          const bool up = (i & k) == 0;
+          if (up ? !i_before_l : i_before_l) {
+            double tk = key[i]; key[i] = key[l]; key[l] = tk;
+            int ti = idx[i]; idx[i] = idx[l]; idx[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    double W = 0;
+    for (int i = 0; i < n; i++) W += key[i] > 0 ? key[i] : 0.0;
+    int r = n;
+    if (cutoff > 0) {
+      double tail = 0;
+      r = 1;
+      for (int i = n - 1; i >= 1; i--) {
+        tail += key[i] > 0 ? key[i] : 0.0;
+        if (tail > cutoff * W) { r = i + 1; break; }
+      }
+    }
+    int nz = 0;
+    for (int i = 0; i < n; i++) nz += key[i] > floor2 * key[0] ? 1 : 0;
+    if (nz < r) r = nz;
+    if (r > chi_max) r = chi_max;
+    if (r < 1) r = 1;
+    double kept = 0;
+    for (int i = 0; i < r; i++) kept += key[i] > 0 ? key[i] : 0.0;
+    r_s = r;
+    kept_s = kept;
+    P.res[0] = r;
+    P.res[1] = W > 0 ? kept / W : 1.0;
+    P.res[2] = W;
+    P.res[3] = kept;
+  }
+  __syncthreads();
+  const int r = r_s;
+  const double kept = kept_s;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    P.perm[i] = idx[i];
+    P.lam_out[i] = kept > 0 ? sqrt(fmax(key[i], 0.0) / kept) : 0.0;
+  }
+}
+
+cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff,
+                          double floor2, cudaStream_t s) {
+  if (n_probs <= 0) return cudaSuccess;
+  const size_t sm = SEL_MAX * (sizeof(double) + sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_select<<<n_probs, 1024, sm, s>>>(d_probs, chi_max, cutoff, floor2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Write-back gathers: new right site B = (V_r)^dagger and the unweighted
+// remainder Rbar_r = (Mbar V)[:, kept] / sqrt(kept weight).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_gather(const GatherProb* __restrict__ probs) {
+  using CT = typename C2<R>::T;
+  const GatherProb P = probs[blockIdx.y];
+  const long long tot = (long long)P.rows * P.r;
+  const CT* src = (const CT*)P.src;
+  CT* dst = (CT*)P.dst;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (P.mode == 0) {
+      const int mu = (int)(e / P.rows), c = (int)(e % P.rows);
+      dst[e] = cconj(src[(long long)c * P.ld + P.perm[mu]]);
+    } else {
+      const long long row = e / P.r;
+      const int mu = (int)(e % P.r);
+      dst[e] = cscale(src[row * P.ld + P.perm[mu]], P.scale);
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_gather(const GatherProb* d_probs, int n_probs, long long max_elems,
+                          cudaStream_t s) {
+  if (n_probs <= 0 || max_elems <= 0) return cudaSuccess;
+  long long gx = (max_elems + 255) / 256;
+  if (gx > 65535) gx = 65535;
+  k_gather<R><<<dim3((unsigned)gx, n_probs), 256, 0, s>>>(d_probs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gather<float>(const GatherProb*, int, long long, cudaStream_t);
+template cudaError_t launch_gather<double>(const GatherProb*, int, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// One-qubit gates on singleton sites, amplitudes, conversions.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_apply_1q(void* const* __restrict__ sites, const int* __restrict__ cls,
+                           const int* __restrict__ crs, const double* __restrict__ us) {
+  using CT = typename C2<R>::T;
+  const int p = blockIdx.y;
+  const int cl = cls[p], cr = crs[p];
+  CT* S = (CT*)sites[p];
+  const double* u = us + 8 * p;
+  const CT u00 = cmk<CT>(u[0], u[1]), u01 = cmk<CT>(u[2], u[3]);
+  const CT u10 = cmk<CT>(u[4], u[5]), u11 = cmk<CT>(u[6], u[7]);
+  const long long tot = (long long)cl * cr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long a = e / cr, b = e % cr;
+    const long long i0 = (a * 2) * cr + b, i1 = (a * 2 + 1) * cr + b;
+    const CT x0 = S[i0], x1 = S[i1];
+    CT y0 = cmul(u00, x0), y1 = cmul(u10, x0);
+    cfma(y0, u01, x1);
+    cfma(y1, u11, x1);
+    S[i0] = y0;
+    S[i1] = y1;
+  }
+}
+
+template <typename R>
+cudaError_t launch_apply_1q(void* const* d_sites, const int* d_cl, const int* d_cr,
+                            const double* d_u, int n_sites, long long max_elems, cudaStream_t s) {
+  if (n_sites <= 0) return cudaSuccess;
+  long long gx = (max_elems + 255) / 256;
+  if (gx > 65535) gx = 65535;
+  if (gx < 1) gx = 1;
+  k_apply_1q<R><<<dim3((unsigned)gx, n_sites), 256, 0, s>>>(d_sites, d_cl, d_cr, d_u);
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply_1q<float>(void* const*, const int*, const int*, const double*,
+                                            int, long long, cudaStream_t);
+template cudaError_t launch_apply_1q<double>(void* const*, const int*, const int*, const double*,
+                                             int, long long, cudaStream_t);
+
+template <typename R>
+__global__ void k_amp_step(const double2* __restrict__ vin, double2* __restrict__ vout,
+                           const void* __restrict__ site, int cl, int cr, int bit) {
+  using CT = typename C2<R>::T;
+  const CT* S = (const CT*)site;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cr) return;
+  double2 acc = make_double2(0, 0);
+  for (int a = 0; a < cl; a++) {
+    const CT s = S[((long long)a * 2 + bit) * cr + b];
+    const double2 v = vin[a];
+    acc.x += v.x * (double)s.x - v.y * (double)s.y;
+    acc.y += v.x * (double)s.y + v.y * (double)s.x;
+  }
+  vout[b] = acc;
+}
+
+template <typename R>
+cudaError_t launch_amp_step(const void* v_in, void* v_out, const void* site, int cl, int cr,
+                            int bit, cudaStream_t s) {
+  k_amp_step<R><<<(cr + 127) / 128, 128, 0, s>>>((const double2*)v_in, (double2*)v_out, site, cl,
+                                                 cr, bit);
+  return cudaGetLastError();
+}
+template cudaError_t launch_amp_step<float>(const void*, void*, const void*, int, int, int, cudaStream_t);
+template cudaError_t launch_amp_step<double>(const void*, void*, const void*, int, int, int, cudaStream_t);
+
+template <typename R>
+__global__ void k_from_c128(const double* __restrict__ src, void* __restrict__ dst, long long n) {
+  using CT = typename C2<R>::T;
+  CT* d = (CT*)dst;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = cmk<CT>(src[2 * i], src[2 * i + 1]);
+}
+template <typename R>
+__global__ void k_to_c128(const void* __restrict__ src, double* __restrict__ dst, long long n) {
+  using CT = typename C2<R>::T;
+  const CT* s = (const CT*)src;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    dst[2 * i] = s[i].x;
+    dst[2 * i + 1] = s[i].y;
+  }
+}
+template <typename R>
+cudaError_t launch_convert_from_c128(const double* src, void* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long g = (n + 255) / 256;
+  k_from_c128<R><<<(unsigned)(g > 8192 ? 8192 : g), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_convert_to_c128(const void* src, double* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long g = (n + 255) / 256;
+  k_to_c128<R><<<(unsigned)(g > 8192 ? 8192 : g), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert_from_c128<float>(const double*, void*, long long, cudaStream_t);
+template cudaError_t launch_convert_from_c128<double>(const double*, void*, long long, cudaStream_t);
+template cudaError_t launch_convert_to_c128<float>(const void*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert_to_c128<double>(const void*, double*, long long, cudaStream_t);
+
+}  // namespace ctebd

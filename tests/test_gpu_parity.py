@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA cluster update against the FP64 CPU oracle.
+
+Tolerances (written per test): FP64 runs reproduce the oracle to 1e-12 where
+nothing is truncated (the state-vector bound for n <= 16) and to 1e-10 in the
+per-split fidelities when something is.  FP32 runs meet the stated targets:
+|<psi_gpu|psi_ref>| >= 1 - 1e-6 and per-split f_j within 1e-5 relative; bond
+dimensions (integers decided by floating point) are compared where the
+truncation decision is not at the noise level of the precision.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import (as_oracle, contracted, download, entangling_circuit, lib,
+                         random_unitary, run_gpu, statevector_of)
+
+pytestmark = pytest.mark.gpu
+W1 = synth.WORKLOADS[1]
+
+
+@pytest.mark.parametrize("sample", range(3))
+def test_cfg1_fp64_matches_statevector(sample):
+    P = lib()
+    c = W1.circuit(sample, 1)
+    mps, log = run_gpu(c, W1.chi_max, W1.cutoff, W1.q_max, 0, W1.k_max, P.FP64)
+    ref = oracle.simulate(c, W1.chi_max, W1.cutoff, W1.q_max, 0, W1.k_max)
+    chi, sites, lams = download(mps)
+    assert list(chi) == list(ref.chi())
+    psi = oracle.statevector(c)
+    sv = statevector_of(sites)
+    assert np.abs(sv - psi).max() <= 1e-12
+    assert abs(np.vdot(psi, sv)) >= 1 - 1e-12
+    for b in range(1, c.n_qubits):
+        np.testing.assert_allclose(lams[b], ref.lam(b), atol=1e-12)
+    assert abs(mps.fidelity() - 1) < 1e-12
+    # the library's own amplitude kernel
+    rng = np.random.default_rng(sample)
+    for _ in range(5):
+        bits = rng.integers(0, 2, c.n_qubits)
+        idx = int("".join(map(str, bits)), 2)
+        assert abs(mps.amplitude(bits) - psi[idx]) < 1e-12
+
+
+def test_cfg1_fp32_matches_statevector():
+    P = lib()
+    c = W1.circuit(1, 1)
+    mps, _ = run_gpu(c, W1.chi_max, W1.cutoff, W1.q_max, 0, W1.k_max, P.FP32)
+    ref = oracle.simulate(c, W1.chi_max, W1.cutoff, W1.q_max, 0, W1.k_max)
+    chi, sites, _ = download(mps)
+    assert list(chi) == list(ref.chi())
+    psi = oracle.statevector(c)
+    sv = statevector_of(sites)
+    assert abs(np.vdot(psi, sv)) >= 1 - 1e-6
+    assert np.abs(sv - psi).max() < 1e-5
+
+
+@pytest.mark.parametrize("precision,ftol,otol", [(0, 1e-10, 1e-10), (1, 1e-5, 1e-6)])
+def test_truncated_run_matches_oracle(precision, ftol, otol):
+    c = entangling_circuit(12, 24, seed=0)
+    args = (8, 1e-3, 10, 0, 4)
+    mps, log = run_gpu(c, *args, precision)
+    ref = oracle.simulate(c, *args)
+    assert list(mps.bond_dims()) == list(ref.chi())
+    f_gpu = np.concatenate([f for (_, _, _, f) in log])
+    f_ref = ref.split_log()[:, 7]
+    assert len(f_gpu) == len(f_ref)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=ftol)
+    assert abs(mps.fidelity() - np.exp(ref.logF)) <= ftol * 10
+    ov = abs(ref.overlap(as_oracle(mps)))
+    assert ov >= 1 - otol
+
+
+@pytest.mark.parametrize("chi_max", [256, 32])
+def test_cfg2_shape_reduced_fp32(chi_max):
+    """cfg2 statistics (long-range SWAP routing, 10% T) at n=20, 110 layers;
+    chi_max=256 stays exact, chi_max=32 truncates."""
+    P = lib()
+    w = synth.reduced(2, 20, 110)
+    c = w.circuit(0, 2)
+    args = (chi_max, w.cutoff, w.q_max, 0, w.k_max)
+    mps, log = run_gpu(c, *args, P.FP32)
+    ref = oracle.simulate(c, *args)
+    assert list(mps.bond_dims()) == list(ref.chi())
+    ov = abs(ref.overlap(as_oracle(mps)))
+    assert ov >= 1 - 1e-6
+    f_gpu = np.concatenate([f for (_, _, _, f) in log])
+    np.testing.assert_allclose(f_gpu, ref.split_log()[:, 7], rtol=1e-5)
+    assert abs(mps.fidelity() / np.exp(ref.logF) - 1) <= 1e-5
+
+
+def test_clifford_reduced_tableau():
+    """cfg3 statistics at n=30, 100 layers: chi_b = 2^{S_b} (stabilizer tableau), flat spectra."""
+    P = lib()
+    w = synth.reduced(3, 30, 100)
+    c = w.circuit(0, 3)
+    mps, _ = run_gpu(c, w.chi_max, w.cutoff, w.q_max, 0, w.k_max, P.FP32)
+    S = oracle.stabilizer_entropies(c)
+    assert list(mps.bond_dims()) == [2 ** s for s in S]
+    for b in range(1, 30):
+        np.testing.assert_allclose(mps.lam(b), 2.0 ** (-S[b] / 2), rtol=1e-5)
+    assert abs(mps.fidelity() - 1) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("q0,k", [(0, 2), (1, 4), (3, 3), (4, 2)])
+def test_single_cluster_update_matches_oracle(precision, q0, k):
+    P = lib()
+    n, chi = 6, 16
+    chis, sites, lams = synth.random_right_canonical(n, chi, seed=10 * q0 + k)
+    rng = np.random.default_rng(q0 + 7 * k)
+    U = random_unitary(1 << k, rng)
+    cfg = P.make_config(n, chi, 1e-6, 2 + 2 * 4 + 8, 0, 0, precision)
+    m = P.MPS(cfg)
+    m.load(chis, sites, lams)
+    cl = P.Cluster(q0, k, 0, 1)
+    m.apply_cluster(cl, U)
+    f = m.truncate_split(cl)
+    ref = oracle.MPS.from_arrays(sites, lams)
+    f_ref, r_ref = ref.cluster_update(q0, k, U, chi, 1e-6)
+    tol = 1e-10 if precision == 0 else 1e-5
+    np.testing.assert_allclose(f, f_ref, rtol=tol)
+    chi_g = m.bond_dims()
+    assert list(chi_g) == list(ref.chi())
+    for b in range(q0 + 1, q0 + k):
+        np.testing.assert_allclose(m.lam(b), ref.lam(b), atol=tol)
+    got = contracted([m.site(q) for q in range(n)], q0, k)
+    want = contracted([ref.site(q) for q in range(n)], q0, k)
+    np.testing.assert_allclose(got, want, atol=tol * 10)
+    for q in range(q0 + 1, q0 + k):          # new right sites are right isometries
+        B = m.site(q).reshape(chi_g[q], -1)
+        np.testing.assert_allclose(B @ B.conj().T, np.eye(chi_g[q]), atol=tol * 10)
+
+
+def test_step_batched_equals_one_by_one():
+    P = lib()
+    n, chi = 12, 8
+    chis, sites, lams = synth.random_right_canonical(n, chi, seed=3)
+    rng = np.random.default_rng(0)
+    clusters = [P.Cluster(0, 2, 0, 1), P.Cluster(3, 4, 0, 1), P.Cluster(8, 3, 0, 1)]
+    Us = [random_unitary(1 << c.k, rng) for c in clusters]
+    cfg = P.make_config(n, chi, 1e-8, 20, 0, 0, P.FP64)
+    a = P.MPS(cfg)
+    a.load(chis, sites, lams)
+    fa = a.step(clusters, Us)
+    b = P.MPS(cfg)
+    b.load(chis, sites, lams)
+    fb = []
+    for c, U in zip(clusters, Us):
+        b.apply_cluster(c, U)
+        fb.extend(b.truncate_split(c))
+    np.testing.assert_allclose(fa, fb, rtol=1e-12)
+    assert list(a.bond_dims()) == list(b.bond_dims())
+    for q in range(n):
+        np.testing.assert_allclose(a.site(q), b.site(q), atol=1e-12)
+
+
+def test_api_state_errors():
+    P = lib()
+    cfg = P.make_config(4, 4, 0.0, 10, 0, 0, P.FP64)
+    m = P.MPS(cfg)
+    with pytest.raises(P.CtebdError, match="pending"):
+        m.truncate_split(P.Cluster(0, 2, 0, 1))
+    with pytest.raises(P.CtebdError, match="overlap"):
+        m.step([P.Cluster(0, 2, 0, 1), P.Cluster(1, 2, 0, 1)], [np.eye(4), np.eye(4)])
+    with pytest.raises(P.CtebdError):
+        m.apply_cluster(P.Cluster(3, 2, 0, 1), np.eye(4))      # out of range
