@@ -287,6 +287,7 @@ struct Work {
   size_t bufElems = 0;
   void* G = nullptr;
   void* V = nullptr;
+  void* W = nullptr;     // refinement accumulator
   void* J = nullptr;
   size_t eigElems = 0, jElems = 0;
   double* rho = nullptr;
@@ -380,7 +381,7 @@ struct ctebd_mps {
   void* arena = nullptr;
   size_t arena_cap = 0;
   Staging stage;
-  double* h_res = nullptr;       // pinned results of select (4 per problem)
+  double* h_res = nullptr;       // pinned results of select (8 per problem)
   size_t h_res_cap = 0;
   std::map<int, Work> pending;
   Prof prof;
@@ -431,7 +432,7 @@ extern "C" int mps_create(const ctebd_config* cfg, void* cuda_stream, ctebd_mps*
   m->lam.assign(m->n + 1, nullptr);
   int rc = m->stage.init(8 << 20, m->stream);
   if (rc) { mps_destroy(m); return rc; }
-  if (cudaMallocHost(&m->h_res, 4 * sizeof(double) * 4096) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "pinned"); }
+  if (cudaMallocHost(&m->h_res, 8 * sizeof(double) * 4096) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "pinned"); }
   m->h_res_cap = 4096;
   std::vector<double> one(1, 1.0);
   for (int b = 0; b <= m->n; b++) {
@@ -460,7 +461,7 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   if (m->stream) cudaStreamSynchronize(m->stream);
   for (auto& kv : m->pending) {
     Work& w = kv.second;
-    if (w.owned) { cudaFree(w.bufA); cudaFree(w.bufB); cudaFree(w.G); cudaFree(w.V); cudaFree(w.J); cudaFree(w.rho); cudaFree(w.perm); cudaFree(w.res); }
+    if (w.owned) { cudaFree(w.bufA); cudaFree(w.bufB); cudaFree(w.G); cudaFree(w.V); cudaFree(w.W); cudaFree(w.J); cudaFree(w.rho); cudaFree(w.perm); cudaFree(w.res); }
   }
   for (void* p : m->site) if (p) cudaFree(p);
   for (double* p : m->lam) if (p) cudaFree(p);
@@ -524,7 +525,7 @@ static int carve_work(ctebd_mps* m, std::vector<Work>& ws) {
   auto al = [](size_t b) { return round_up(b, 256); };
   for (auto& w : ws) {
     work_sizes(m, w);
-    total += 2 * al(w.bufElems * m->esz) + 2 * al(w.eigElems * m->esz) + al(w.jElems * m->esz) +
+    total += 2 * al(w.bufElems * m->esz) + 3 * al(w.eigElems * m->esz) + al(w.jElems * m->esz) +
              al(w.nmax * 8) + al(w.nmax * 4) + al(64);
   }
   if (total > m->arena_cap) {
@@ -545,6 +546,7 @@ static int carve_work(ctebd_mps* m, std::vector<Work>& ws) {
     w.bufB = p; p += al(w.bufElems * m->esz);
     w.G = p; p += al(w.eigElems * m->esz);
     w.V = p; p += al(w.eigElems * m->esz);
+    w.W = p; p += al(w.eigElems * m->esz);
     w.J = p; p += al(w.jElems * m->esz);
     w.rho = (double*)p; p += al(w.nmax * 8);
     w.perm = (int*)p; p += al(w.nmax * 4);
@@ -563,6 +565,7 @@ static int alloc_owned(ctebd_mps* m, Work& w) {
   TRY(A(&w.bufB, w.bufElems * m->esz));
   TRY(A(&w.G, w.eigElems * m->esz));
   TRY(A(&w.V, w.eigElems * m->esz));
+  TRY(A(&w.W, w.eigElems * m->esz));
   TRY(A(&w.J, w.jElems * m->esz));
   TRY(A((void**)&w.rho, w.nmax * 8));
   TRY(A((void**)&w.perm, w.nmax * 4));
@@ -573,7 +576,7 @@ static int alloc_owned(ctebd_mps* m, Work& w) {
 
 static void free_owned(ctebd_mps* m, Work& w) {
   if (!w.owned) return;
-  for (void* p : {w.bufA, w.bufB, w.G, w.V, w.J, (void*)w.rho, (void*)w.perm, (void*)w.res})
+  for (void* p : {w.bufA, w.bufB, w.G, w.V, w.W, w.J, (void*)w.rho, (void*)w.perm, (void*)w.res})
     if (p) cudaFreeAsync(p, m->stream);
   w.owned = false;
 }
@@ -634,184 +637,269 @@ static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<co
   return CTEBD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Split pieces (one level = one bond per active cluster)
+// ---------------------------------------------------------------------------
+struct Level {
+  std::vector<int> act;                        // indices into ws
+  std::vector<int> mm, nn, npad, nbv, shift;   // per active problem
+};
+
+// G = Z^H diag(lambda_L^2) Z for Z = bufA (Mbar) or bufB (Mbar V)
+static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
+                      bool from_rotated) {
+  std::vector<GemmProb> probs;
+  for (int a : sel) {
+    Work& w = ws[L.act[a]];
+    CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)L.npad[a] * L.npad[a] * m->esz, m->stream));
+    GemmProb p{};
+    const void* Z = from_rotated ? w.bufB : w.bufA;
+    p.M = L.nn[a]; p.N = L.nn[a]; p.K = L.mm[a]; p.batch = 1;
+    p.A = Z; p.lda = L.nn[a]; p.opA = 1;
+    p.B = Z; p.ldb = L.nn[a]; p.opB = 0;
+    p.C = w.G; p.ldc = L.npad[a];
+    p.kw = m->lam[w.q0];
+    p.kw_shift = L.shift[a];
+    p.alpha = 1.0;
+    probs.push_back(p);
+  }
+  return run_gemms(m, probs, KK_GEMM_GRAM);
+}
+
+// Batched block-Jacobi on every G of the selection; rotations accumulate
+// into acc[a] (set to identity first).  floor_factor scales the absolute
+// rotation floor eps * trace(G): 1 for a Gram computed from Mbar (absolute
+// rounding), ~0 for a Gram of already rotated columns (relative accuracy).
+static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
+                     const std::vector<void*>& acc, double floor_factor) {
+  const bool f64 = m->fp64;
+  const int JB = eig_block(f64);
+  const int na = (int)sel.size();
+  if (na == 0) return CTEBD_OK;
+  std::vector<EigProb> eps(na);
+  double* d_off = nullptr;
+  CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * 3 * na, m->stream));
+  int max_npad = 0, max_nb = 0;
+  for (int i = 0; i < na; i++) {
+    const int a = sel[i];
+    Work& w = ws[L.act[a]];
+    eps[i].G = w.G; eps[i].V = acc[i]; eps[i].J = w.J;
+    eps[i].npad = L.npad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
+    eps[i].off = d_off + 2 * i;
+    eps[i].scale = d_off + 2 * na + i;
+    eps[i].floor_factor = floor_factor;
+    max_npad = std::max(max_npad, L.npad[a]);
+    max_nb = std::max(max_nb, L.nbv[a]);
+  }
+  const EigProb* dep;
+  TRY(m->stage.push(eps.data(), eps.size(), &dep));
+  {
+    ProfScope ps(m->prof, m->stream, KK_EIG_INIT, 0, 0);
+    CUDA_TRY(f64 ? launch_eig_init<double>(dep, na, max_npad, m->stream)
+                 : launch_eig_init<float>(dep, na, max_npad, m->stream));
+    CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
+  }
+  std::vector<double> hoff(2 * na);
+  const int max_sweeps = 30;
+  for (int sweep = 0; sweep < max_sweeps; sweep++) {
+    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 2 * na, m->stream));
+    for (int t = 0; t < max_nb - 1; t++) {
+      double bin = 0, fap = 0, bap = 0;
+      const double D = 2.0 * JB;
+      for (int i = 0; i < na; i++) {
+        const int a = sel[i];
+        if (!eps[i].active || t >= L.nbv[a] - 1) continue;
+        const double h = L.nbv[a] / 2, np2 = (double)L.npad[a] * L.npad[a];
+        bin += 2 * h * D * D * m->esz;                           // read blocks, write J
+        fap += 8.0 * (2 * h * (h + 1) / 2 + h * h) * D * D * D;  // J^H G J (upper tiles), V J
+        bap += (4 * np2 + h * D * D) * m->esz;                   // G, V read+write, J read
+      }
+      {
+        ProfScope ps(m->prof, m->stream, KK_EIG_INNER, 0, bin);
+        CUDA_TRY(f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
+                     : launch_eig_inner<float>(dep, na, max_nb, t, m->stream));
+      }
+      {
+        ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, fap, bap);
+        CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
+                     : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    bool any = false;
+    for (int i = 0; i < na; i++) {
+      // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
+      m->prof.flops[KK_EIG_INNER] += hoff[2 * i + 1] * 42.0 * (2 * JB);
+      if (!eps[i].active) continue;
+      if (hoff[2 * i] == 0.0) eps[i].active = 0; else any = true;
+    }
+    if (!any) break;
+    m->stage.reset();
+    TRY(m->stage.push(eps.data(), eps.size(), &dep));
+  }
+  CUDA_TRY(cudaFreeAsync(d_off, m->stream));
+  return CTEBD_OK;
+}
+
+// Rfull = Mbar V (bufB), rho = weighted column norms, then truncation select
+static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level& L,
+                                const std::vector<int>& sel) {
+  const bool f64 = m->fp64;
+  const double floor_rel = f64 ? 1e-13 : 1e-6;
+  const int na = (int)sel.size();
+  if (na == 0) return CTEBD_OK;
+  std::vector<GemmProb> probs;
+  int max_n = 0, max_m = 0;
+  for (int a : sel) {
+    Work& w = ws[L.act[a]];
+    GemmProb p{};
+    p.M = L.mm[a]; p.N = L.nn[a]; p.K = L.nn[a]; p.batch = 1;
+    p.A = w.bufA; p.lda = L.nn[a]; p.opA = 0;
+    p.B = w.V; p.ldb = L.npad[a]; p.opB = 0;
+    p.C = w.bufB; p.ldc = L.nn[a]; p.alpha = 1.0;
+    probs.push_back(p);
+    CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * L.nn[a], m->stream));
+    max_n = std::max(max_n, L.nn[a]);
+    max_m = std::max(max_m, L.mm[a]);
+  }
+  TRY(run_gemms(m, probs, KK_GEMM_PROJ));
+  {
+    std::vector<const void*> R(na);
+    std::vector<const double*> Lm(na);
+    std::vector<double*> rho(na);
+    std::vector<int> mm(na), nn(na), sh(na);
+    double by = 0;
+    for (int i = 0; i < na; i++) {
+      const int a = sel[i];
+      Work& w = ws[L.act[a]];
+      R[i] = w.bufB; Lm[i] = m->lam[w.q0]; rho[i] = w.rho;
+      mm[i] = L.mm[a]; nn[i] = L.nn[a]; sh[i] = L.shift[a];
+      by += (double)mm[i] * nn[i] * m->esz;
+    }
+    const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
+    TRY(m->stage.push(R.data(), na, (const void* const**)&dR));
+    TRY(m->stage.push(mm.data(), na, &dm));
+    TRY(m->stage.push(nn.data(), na, &dn));
+    TRY(m->stage.push(sh.data(), na, &dsh));
+    TRY(m->stage.push(Lm.data(), na, (const double* const**)&dL));
+    TRY(m->stage.push(rho.data(), na, (double* const**)&drho));
+    ProfScope ps(m->prof, m->stream, KK_COLNORM, 0, by);
+    CUDA_TRY(f64 ? launch_colnorm_batch<double>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream)
+                 : launch_colnorm_batch<float>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream));
+  }
+  std::vector<SelProb> sp(na);
+  for (int i = 0; i < na; i++) {
+    const int a = sel[i];
+    Work& w = ws[L.act[a]];
+    sp[i].rho = w.rho; sp[i].n = L.nn[a]; sp[i].perm = w.perm;
+    sp[i].lam_out = m->lam[w.q0 + L.shift[a]]; sp[i].res = w.res;
+    if (L.nn[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
+  }
+  const SelProb* dsp;
+  TRY(m->stage.push(sp.data(), na, &dsp));
+  {
+    ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
+    CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, floor_rel * floor_rel, m->stream));
+  }
+  // results land at the level-local index a (h_res[8 a .. 8 a + 7])
+  if (L.act.size() > m->h_res_cap) return fail(CTEBD_ERR_ARG, "too many clusters");
+  for (int a : sel)
+    CUDA_TRY(cudaMemcpyAsync(m->h_res + 8 * a, ws[L.act[a]].res, 8 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->stage.reset();
+  return CTEBD_OK;
+}
+
 // k-1 splits, right to left (Fig. 2 with the truncation of Fig. 3)
 static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::vector<double>>& fs) {
   const bool f64 = m->fp64;
   const int JB = eig_block(f64);
-  const double floor_rel = f64 ? 1e-13 : 1e-6;
   fs.assign(ws.size(), {});
   int kmax = 0;
   for (auto& w : ws) kmax = std::max(kmax, w.k);
   for (int lev = 1; lev < kmax; lev++) {
-    std::vector<int> act;
-    for (size_t i = 0; i < ws.size(); i++) if (ws[i].k - 1 >= lev) act.push_back((int)i);
-    if (act.empty()) break;
-    const int na = (int)act.size();
-    std::vector<int> mm(na), nn(na), npad(na), nbv(na), shift(na);
-    int max_npad = 0, max_nb = 0, max_n = 0, max_m = 0;
+    Level L;
+    for (size_t i = 0; i < ws.size(); i++) if (ws[i].k - 1 >= lev) L.act.push_back((int)i);
+    if (L.act.empty()) break;
+    const int na = (int)L.act.size();
+    L.mm.resize(na); L.nn.resize(na); L.npad.resize(na); L.nbv.resize(na); L.shift.resize(na);
+    std::vector<int> all(na);
     for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
+      Work& w = ws[L.act[a]];
       const int j = w.k - lev;  // bond q0 + j is split off
-      mm[a] = w.chiL << j;
-      nn[a] = 2 * w.rdim;
-      shift[a] = j;
-      npad[a] = (int)round_up(nn[a], 2 * JB);
-      nbv[a] = npad[a] / JB;
-      max_npad = std::max(max_npad, npad[a]);
-      max_nb = std::max(max_nb, nbv[a]);
-      max_n = std::max(max_n, nn[a]);
-      max_m = std::max(max_m, mm[a]);
-      if ((size_t)npad[a] * npad[a] > w.eigElems) return fail(CTEBD_ERR_ARG, "internal: eig buffer");
-      CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)npad[a] * npad[a] * m->esz, m->stream));
-      CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * nn[a], m->stream));
+      L.mm[a] = w.chiL << j;
+      L.nn[a] = 2 * w.rdim;
+      L.shift[a] = j;
+      L.npad[a] = (int)round_up(L.nn[a], 2 * JB);
+      L.nbv[a] = L.npad[a] / JB;
+      all[a] = a;
+      if ((size_t)L.npad[a] * L.npad[a] > w.eigElems) return fail(CTEBD_ERR_ARG, "internal: eig buffer");
     }
-    // Gram G = Mbar^H diag(lambda_L^2) Mbar
-    std::vector<GemmProb> probs;
-    for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
-      GemmProb p{};
-      p.M = nn[a]; p.N = nn[a]; p.K = mm[a]; p.batch = 1;
-      p.A = w.bufA; p.lda = nn[a]; p.opA = 1;
-      p.B = w.bufA; p.ldb = nn[a]; p.opB = 0;
-      p.C = w.G; p.ldc = npad[a];
-      p.kw = m->lam[w.q0];
-      p.kw_shift = shift[a];
-      p.alpha = 1.0;
-      probs.push_back(p);
-    }
-    TRY(run_gemms(m, probs, KK_GEMM_GRAM));
-    // eigen-decomposition of every G
-    std::vector<EigProb> eps(na);
-    double* d_off = nullptr;
-    CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * 2 * na, m->stream));
-    for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
-      eps[a].G = w.G; eps[a].V = w.V; eps[a].J = w.J;
-      eps[a].npad = npad[a]; eps[a].nb = nbv[a]; eps[a].active = 1;
-      eps[a].off = d_off + 2 * a;
-    }
-    const EigProb* dep;
-    TRY(m->stage.push(eps.data(), eps.size(), &dep));
-    {
-      ProfScope ps(m->prof, m->stream, KK_EIG_INIT, 0, 0);
-      CUDA_TRY(f64 ? launch_eig_init<double>(dep, na, max_npad, m->stream)
-                   : launch_eig_init<float>(dep, na, max_npad, m->stream));
-    }
-    std::vector<double> hoff(2 * na);
-    const int max_sweeps = 30;
-    for (int sweep = 0; sweep < max_sweeps; sweep++) {
-      CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 2 * na, m->stream));
-      for (int t = 0; t < max_nb - 1; t++) {
-        // algorithmic work of this round over the problems still active
-        double fin = 0, bin = 0, fap = 0, bap = 0;
-        const double D = 2.0 * JB;
-        for (int a = 0; a < na; a++) {
-          if (!eps[a].active || t >= nbv[a] - 1) continue;
-          const double h = nbv[a] / 2, np2 = (double)npad[a] * npad[a];
-          bin += 2 * h * D * D * m->esz;                  // read blocks, write J
-          fap += 24.0 * h * h * D * D * D;                 // J^H G J and V J (2 + 1 complex GEMMs)
-          bap += (4 * np2 + h * D * D) * m->esz;           // G, V read+write, J read
-        }
-        {
-          ProfScope ps(m->prof, m->stream, KK_EIG_INNER, fin, bin);
-          CUDA_TRY(f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
-                       : launch_eig_inner<float>(dep, na, max_nb, t, m->stream));
-        }
-        {
-          ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, fap, bap);
-          CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
-                       : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
-        }
-      }
-      CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, m->stream));
-      CUDA_TRY(cudaStreamSynchronize(m->stream));
-      bool any = false;
+    // pass 1: Schmidt-weighted Gram of Mbar, its eigenvectors V, weights rho
+    TRY(level_gram(m, ws, L, all, false));
+    std::vector<void*> accV(na);
+    for (int a = 0; a < na; a++) accV[a] = ws[L.act[a]].V;
+    TRY(level_eig(m, ws, L, all, accV, 1.0));
+    TRY(level_project_select(m, ws, L, all));
+    // pass 2 (FP32 only): where the cutoff or the zero floor -- not chi_max --
+    // decided the rank, the weights of the small directions must be accurate
+    // relative to their own size: re-diagonalise the freshly computed Gram of
+    // the rotated columns Z = M V and rotate V and Z by the result.
+    if (!f64) {
+      std::vector<int> ref;
       for (int a = 0; a < na; a++) {
-        if (!eps[a].active) continue;
-        if (hoff[2 * a] == 0.0) eps[a].active = 0; else any = true;
+        const int r = (int)m->h_res[8 * a];
+        if (r < std::min(m->cfg.chi_max, L.nn[a])) ref.push_back(a);
       }
-      if (!any) break;
-      m->stage.reset();
-      TRY(m->stage.push(eps.data(), eps.size(), &dep));
-    }
-    CUDA_TRY(cudaFreeAsync(d_off, m->stream));
-    // Rfull = Mbar V (bufB), weighted column norms rho
-    probs.clear();
-    for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
-      GemmProb p{};
-      p.M = mm[a]; p.N = nn[a]; p.K = nn[a]; p.batch = 1;
-      p.A = w.bufA; p.lda = nn[a]; p.opA = 0;
-      p.B = w.V; p.ldb = npad[a]; p.opB = 0;
-      p.C = w.bufB; p.ldc = nn[a]; p.alpha = 1.0;
-      probs.push_back(p);
-    }
-    TRY(run_gemms(m, probs, KK_GEMM_PROJ));
-    {
-      std::vector<const void*> R(na);
-      std::vector<const double*> L(na);
-      std::vector<double*> rho(na);
-      for (int a = 0; a < na; a++) {
-        Work& w = ws[act[a]];
-        R[a] = w.bufB; L[a] = m->lam[w.q0]; rho[a] = w.rho;
+      if (!ref.empty()) {
+        TRY(level_gram(m, ws, L, ref, true));
+        std::vector<void*> accW(ref.size());
+        for (size_t i = 0; i < ref.size(); i++) accW[i] = ws[L.act[ref[i]]].W;
+        TRY(level_eig(m, ws, L, ref, accW, 1e-12));
+        // V <- V W (into G, then swap), Rfull recomputed from the new V
+        std::vector<GemmProb> probs;
+        for (int a : ref) {
+          Work& w = ws[L.act[a]];
+          GemmProb p{};
+          p.M = L.nn[a]; p.N = L.nn[a]; p.K = L.nn[a]; p.batch = 1;
+          p.A = w.V; p.lda = L.npad[a]; p.opA = 0;
+          p.B = w.W; p.ldb = L.npad[a]; p.opB = 0;
+          p.C = w.G; p.ldc = L.npad[a]; p.alpha = 1.0;
+          probs.push_back(p);
+        }
+        TRY(run_gemms(m, probs, KK_GEMM_PROJ));
+        for (int a : ref) std::swap(ws[L.act[a]].V, ws[L.act[a]].G);
+        TRY(level_project_select(m, ws, L, ref));
       }
-      const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
-      TRY(m->stage.push(R.data(), na, (const void* const**)&dR));
-      TRY(m->stage.push(mm.data(), na, &dm));
-      TRY(m->stage.push(nn.data(), na, &dn));
-      TRY(m->stage.push(shift.data(), na, &dsh));
-      TRY(m->stage.push(L.data(), na, (const double* const**)&dL));
-      TRY(m->stage.push(rho.data(), na, (double* const**)&drho));
-      double by = 0;
-      for (int a = 0; a < na; a++) by += (double)mm[a] * nn[a] * m->esz;
-      ProfScope ps(m->prof, m->stream, KK_COLNORM, 0, by);
-      CUDA_TRY(f64 ? launch_colnorm_batch<double>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream)
-                   : launch_colnorm_batch<float>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream));
     }
-    // truncation select: lambda of bond q0+j written in place
-    std::vector<SelProb> sp(na);
-    for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
-      const int j = w.k - lev;
-      sp[a].rho = w.rho; sp[a].n = nn[a]; sp[a].perm = w.perm;
-      sp[a].lam_out = m->lam[w.q0 + j]; sp[a].res = w.res;
-      if (nn[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
-    }
-    const SelProb* dsp;
-    TRY(m->stage.push(sp.data(), na, &dsp));
-    {
-      ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
-      CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, floor_rel * floor_rel, m->stream));
-    }
-    if ((size_t)na > m->h_res_cap) return fail(CTEBD_ERR_ARG, "too many clusters");
-    for (int a = 0; a < na; a++)
-      CUDA_TRY(cudaMemcpyAsync(m->h_res + 4 * a, ws[act[a]].res, 4 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-    CUDA_TRY(cudaStreamSynchronize(m->stream));
-    m->stage.reset();
     // write back: new right sites, unweighted remainders
     std::vector<GatherProb> gp;
     long long maxe = 0;
     for (int a = 0; a < na; a++) {
-      Work& w = ws[act[a]];
+      Work& w = ws[L.act[a]];
       const int j = w.k - lev;
-      const int r = (int)m->h_res[4 * a];
-      const double f = m->h_res[4 * a + 1], W = m->h_res[4 * a + 2], kept = m->h_res[4 * a + 3];
+      const double* res = m->h_res + 8 * a;   // level-local index, as written by the select
+      const int r = (int)res[0];
+      const double f = res[1], W = res[2], kept = res[3];
       if (!(kept > 0) || !std::isfinite(W)) return fail(CTEBD_ERR_NUMERIC, "split: non-finite or zero weight");
+      if (r < 1 || r > L.nn[a] || r > m->cfg.chi_max || r > L.mm[a] * 1LL * L.nn[a])
+        return fail(CTEBD_ERR_NUMERIC, "split: rank out of range (" + std::to_string(r) + ")");
       const int bnd = w.q0 + j;
-      TRY(ensure_site(m, bnd, (size_t)r * nn[a]));
+      TRY(ensure_site(m, bnd, (size_t)r * L.nn[a]));
       GatherProb g0{};
-      g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = nn[a]; g0.r = r; g0.ld = npad[a]; g0.mode = 0;
+      g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = L.nn[a]; g0.r = r; g0.ld = L.npad[a]; g0.mode = 0;
       gp.push_back(g0);
       GatherProb g1{};
-      g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = mm[a]; g1.r = r; g1.ld = nn[a]; g1.mode = 1;
+      g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = L.mm[a]; g1.r = r; g1.ld = L.nn[a]; g1.mode = 1;
       g1.scale = 1.0 / std::sqrt(kept);
       gp.push_back(g1);
-      maxe = std::max(maxe, std::max((long long)r * nn[a], (long long)r * mm[a]));
+      maxe = std::max(maxe, std::max((long long)r * L.nn[a], (long long)r * L.mm[a]));
       m->chi[bnd] = r;
       w.rdim = r;
       m->logF += std::log(f);
-      fs[act[a]].push_back(f);
-      const double row[8] = {(double)w.q0, (double)w.k, (double)bnd, (double)mm[a], (double)nn[a], (double)r, f, W};
+      fs[L.act[a]].push_back(f);
+      const double row[8] = {(double)w.q0, (double)w.k, (double)bnd, (double)L.mm[a], (double)L.nn[a], (double)r, f, W};
       m->splitlog.insert(m->splitlog.end(), row, row + 8);
     }
     const GatherProb* dgp;

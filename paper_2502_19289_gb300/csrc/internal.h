@@ -36,7 +36,9 @@ struct EigProb {
   int npad;
   int nb;       // number of JB-blocks, even
   int active;   // 0: converged, skip
-  double* off;  // [0] off-diagonal Frobenius^2, [1] total Frobenius^2
+  double* off;         // [0] significant rotations this sweep, [1] all rotations
+  const double* scale; // trace of G (noise floor of the rotations)
+  double floor_factor; // absolute rotation floor = eps * trace * floor_factor
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -45,7 +47,7 @@ struct SelProb {
   int n;
   int* perm;           // out: kept column indices, descending rho
   double* lam_out;     // out: renormalised kept spectrum (fp64)
-  double* res;         // out: [0] r, [1] f, [2] W, [3] kept
+  double* res;         // out: [0] r, [1] f, [2] W, [3] kept, [4] rank before chi_max cap
 };
 
 struct GatherProb {
@@ -74,6 +76,8 @@ template <typename R>
 cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round,
                              cudaStream_t s);
 int eig_block(bool fp64);  // JB
+template <typename R>
+cudaError_t launch_eig_trace(const EigProb* d_probs, int n_probs, cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n,

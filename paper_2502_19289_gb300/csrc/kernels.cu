@@ -150,8 +150,11 @@ template cudaError_t launch_gemm<double>(const GemmProb*, const long long*, int,
 // giving a unitary J_p; (2) G <- J^H G J and V <- V J tile by tile.
 // ---------------------------------------------------------------------------
 template <typename R> struct EigCfg;
-template <> struct EigCfg<float> { static constexpr int JB = 32; static constexpr int MAXS = 6; };
-template <> struct EigCfg<double> { static constexpr int JB = 16; static constexpr int MAXS = 8; };
+// MAXS: inner sweeps when the whole matrix is one block pair (nb == 2);
+// with several block pairs one inner sweep per round is enough, the outer
+// sweeps converge the rest.
+template <> struct EigCfg<float> { static constexpr int JB = 32; static constexpr int MAXS = 10; };
+template <> struct EigCfg<double> { static constexpr int JB = 16; static constexpr int MAXS = 12; };
 int eig_block(bool fp64) { return fp64 ? EigCfg<double>::JB : EigCfg<float>::JB; }
 
 // Round-robin (circle method) schedule: N players, round t in [0, N-1), slot i.
@@ -162,13 +165,20 @@ __device__ __forceinline__ void circle(int t, int i, int N, int& a, int& b) {
   if (a > b) { int x = a; a = b; b = x; }
 }
 
+// 2x2 Hermitian Jacobi rotation [[a, g], [g*, d]] -> diagonal.  Rotations
+// whose coupling is below the rounding level (relative 4 eps sqrt(a d), or
+// absolute eps * trace(G)) are skipped; a rotation is "significant" (keeps the
+// sweep loop going) when the relative coupling |g| / sqrt(a d) exceeds
+// sqrt(eps) and |g| is well above the absolute noise floor.
 template <typename R>
-__device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R dmax, R& c, R& s,
-                                            typename C2<R>::T& ph, bool& skip) {
+__device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R floor_abs, R& c, R& s,
+                                            typename C2<R>::T& ph, bool& skip, bool& signif) {
   using CT = typename C2<R>::T;
   const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
   const R ag = sqrt(g.x * g.x + g.y * g.y);
-  skip = !(ag > (R)4 * eps * sqrt(fabs(a * d))) || !(ag > eps * dmax) || ag == (R)0;
+  const R rad = sqrt(fabs(a * d));
+  skip = !(ag > (R)4 * eps * rad) || !(ag > floor_abs) || ag == (R)0;
+  signif = !skip && ag > sqrt(eps) * rad && ag > (R)8 * floor_abs;
   if (skip) { c = 1; s = 0; ph = cmk<CT>(1, 0); return; }
   const R zeta = (d - a) / ((R)2 * ag);
   R t;
@@ -194,8 +204,7 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
   CT* ph = reinterpret_cast<CT*>(sn + JB);
   int* pp = reinterpret_cast<int*>(ph + JB);
   int* pq = pp + JB;
-  __shared__ int nrot;
-  __shared__ R dmax_s;
+  __shared__ int nrot, nsig;
   int I, J;
   circle(round, blockIdx.x, P.nb, I, J);
   const CT* G = (const CT*)P.G;
@@ -206,26 +215,24 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
     A[li * LD + lj] = G[gi * P.npad + gj];
     Q[li * LD + lj] = cmk<CT>(li == lj ? 1 : 0, 0);
   }
+  const R eps_r = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+  const R floor_abs = (R)((double)eps_r * (*P.scale) * P.floor_factor);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    R m = 0;
-    for (int i = 0; i < D; i++) m = fmax(m, fabs(A[i * LD + i].x));
-    dmax_s = m;
-  }
-  __syncthreads();
-  int total = 0;
-  for (int sweep = 0; sweep < EigCfg<R>::MAXS; sweep++) {
-    if (threadIdx.x == 0) nrot = 0;
+  int total = 0, total_sig = 0;
+  const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
+  for (int sweep = 0; sweep < max_sweeps; sweep++) {
+    if (threadIdx.x == 0) { nrot = 0; nsig = 0; }
     __syncthreads();
     for (int r = 0; r < D - 1; r++) {
       if (threadIdx.x < JB) {
         int p, q;
         circle(r, threadIdx.x, D, p, q);
         pp[threadIdx.x] = p; pq[threadIdx.x] = q;
-        R c, s; CT e; bool skip;
-        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], dmax_s, c, s, e, skip);
+        R c, s; CT e; bool skip, sig;
+        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, c, s, e, skip, sig);
         cs[threadIdx.x] = c; sn[threadIdx.x] = s; ph[threadIdx.x] = e;
         if (!skip) atomicAdd(&nrot, 1);
+        if (sig) atomicAdd(&nsig, 1);
       }
       __syncthreads();
       for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of A and Q
@@ -254,12 +261,16 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
     }
     const int nr = nrot;
     total += nr;
+    total_sig += nsig;
     __syncthreads();
     if (nr == 0) break;
   }
   CT* Jo = (CT*)P.J + (long long)blockIdx.x * D * D;
   for (int e = threadIdx.x; e < D * D; e += blockDim.x) Jo[e] = Q[(e / D) * LD + (e % D)];
-  if (threadIdx.x == 0 && total > 0) atomicAdd(P.off, (double)total);
+  if (threadIdx.x == 0 && total > 0) {
+    atomicAdd(P.off, (double)total_sig);
+    atomicAdd(P.off + 1, (double)total);
+  }
 }
 
 template <typename R>
@@ -268,15 +279,23 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, PER = D / 16;
   const EigProb P = probs[blockIdx.y];
   if (!P.active || round >= P.nb - 1) return;
-  const int h = P.nb / 2, nG = h * h;
+  const int h = P.nb / 2, nG = h * (h + 1) / 2, nV = h * h;
   const int tile = blockIdx.x;
-  if (tile >= 2 * nG) return;
+  if (tile >= nG + nV) return;
   extern __shared__ unsigned char smraw[];
   CT* S0 = reinterpret_cast<CT*>(smraw);
   CT* S1 = S0 + D * LD;
   const bool isG = tile < nG;
-  const int Pp = isG ? tile / h : (tile - nG) / h;
-  const int Qp = isG ? tile % h : (tile - nG) % h;
+  int Pp, Qp;
+  if (isG) {   // upper-triangular pair index (Pp <= Qp); G is Hermitian
+    int t = tile, row = 0;
+    while (t >= h - row) { t -= h - row; row++; }
+    Pp = row;
+    Qp = row + t;
+  } else {
+    Pp = (tile - nG) / h;
+    Qp = (tile - nG) % h;
+  }
   int K1, K2, I1 = 0, I2 = 0;
   circle(round, Qp, P.nb, K1, K2);
   if (isG) circle(round, Pp, P.nb, I1, I2);
@@ -343,11 +362,22 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
 #pragma unroll
       for (int j = 0; j < PER; j++) cfma(acc[i][j], a[i], b[j]);
   }
+  __syncthreads();   // all reads of S0 / S1 done
 #pragma unroll
   for (int i = 0; i < PER; i++)
 #pragma unroll
-    for (int j = 0; j < PER; j++)
-      X[grow(ty + 16 * i) * P.npad + gcol(tx + 16 * j)] = acc[i][j];
+    for (int j = 0; j < PER; j++) S0[(ty + 16 * i) * LD + tx + 16 * j] = acc[i][j];
+  __syncthreads();
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+    const int li = e / D, lj = e % D;
+    X[grow(li) * P.npad + gcol(lj)] = S0[li * LD + lj];
+  }
+  if (Pp != Qp) {   // Hermitian mirror tile (Q, P), written row by row
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+      const int li = e / D, lj = e % D;
+      X[gcol(li) * P.npad + grow(lj)] = cconj(S0[lj * LD + li]);
+    }
+  }
 }
 
 template <typename R>
@@ -362,6 +392,33 @@ __global__ void k_eig_init(const EigProb* __restrict__ probs, int max_npad) {
     V[e] = cmk<CT>(i == j ? 1 : 0, 0);
   }
 }
+
+template <typename R>
+__global__ void k_eig_trace(const EigProb* __restrict__ probs) {
+  using CT = typename C2<R>::T;
+  const EigProb P = probs[blockIdx.x];
+  const CT* G = (const CT*)P.G;
+  double acc = 0;
+  for (int i = threadIdx.x; i < P.npad; i += blockDim.x) acc += fabs((double)G[(long long)i * P.npad + i].x);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+    *const_cast<double*>(P.scale) = t;
+  }
+}
+
+template <typename R>
+cudaError_t launch_eig_trace(const EigProb* d_probs, int n_probs, cudaStream_t s) {
+  if (n_probs <= 0) return cudaSuccess;
+  k_eig_trace<R><<<n_probs, 256, 0, s>>>(d_probs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_eig_trace<float>(const EigProb*, int, cudaStream_t);
+template cudaError_t launch_eig_trace<double>(const EigProb*, int, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_eig_init(const EigProb* d_probs, int n_probs, int max_npad, cudaStream_t s) {
@@ -403,7 +460,7 @@ cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, in
   eig_attrs<R>();
   const size_t sm_apply = 2 * sizeof(CT) * D * LD;
   const int h = max_nb / 2;
-  k_eig_apply<R><<<dim3(2 * h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
+  k_eig_apply<R><<<dim3(h * (h + 1) / 2 + h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
   return cudaGetLastError();
 }
 
@@ -516,8 +573,9 @@ __global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ pro
     int nz = 0;
     for (int i = 0; i < n; i++) nz += key[i] > floor2 * key[0] ? 1 : 0;
     if (nz < r) r = nz;
-    if (r > chi_max) r = chi_max;
     if (r < 1) r = 1;
+    P.res[4] = r;
+    if (r > chi_max) r = chi_max;
     double kept = 0;
     for (int i = 0; i < r; i++) kept += key[i] > 0 ? key[i] : 0.0;
     r_s = r;
