@@ -68,6 +68,9 @@ def _load():
         "mps_load_device": [P, C.POINTER(I), C.POINTER(P), C.POINTER(P)],
         "mps_split_log": [P, C.POINTER(D), I, C.POINTER(I)],
         "ctebd_last_error": [C.c_char_p, S],
+        "ctebd_profile": [P, I],
+        "ctebd_profile_read": [P, C.POINTER(D), I, C.POINTER(I)],
+        "ctebd_kernel_name": [I, C.c_char_p, S],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
