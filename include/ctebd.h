@@ -204,6 +204,36 @@ int ctebd_profile(ctebd_mps* mps, int mode);
 int ctebd_profile_read(ctebd_mps* mps, double* rows, int cap, int* n_kinds);
 int ctebd_kernel_name(int kind, char* buf, size_t n);
 
+/* split2_noalloc: the two-site split (apply_cluster + truncate_split for a
+   k = 2 cluster) for callers that cannot allocate device memory while they
+   run -- e.g. a host that owns all device memory through its own pool, or a
+   plugin in a process that forbids cudaMalloc/cudaFree on its hot path
+   (both can synchronise the device and stall other streams).  The paper has
+   no counterpart: this is an integration variant of this library.
+
+   Inputs (device, complex64 / fp64, row-major): theta is the cluster tensor
+   with the gate already applied and WITHOUT the left Schmidt weights,
+   (chi_l, 4, chi_r); lam_l holds the chi_l Schmidt values of the left bond.
+   Outputs (device, caller-allocated): site_l_out (chi_l, 2, r) -- the
+   unweighted left site; site_r_out (r, 2, chi_r) -- the right isometry;
+   lam_out (r doubles) -- the renormalised spectrum of the new bond; host
+   r_out and f_out (Eq. 4).  Capacities: r <= min(chi_max, 2 chi_l, 2 chi_r).
+   Same truncation rule and FP32 arithmetic as the handle path.
+
+   It allocates nothing: its scratch is one file-scope device array of about
+   2.4 MiB inside this library, which every GPU that loads the library holds
+   until the process exits.  chi_l and chi_r are limited to 128 (larger
+   values return CTEBD_ERR_ARG).  The first call on a device resolves the
+   array's device address (cudaGetSymbolAddress) with that device current;
+   make that first call before any stream capture.  Every call shares the
+   array and leaves the previous call's data in it; calls that overlap on the
+   GPU (other streams or threads) race on it.  The call synchronises
+   cuda_stream (NULL: the legacy default stream) before returning.
+   Errors: ARG, CUDA, NUMERIC. */
+int split2_noalloc(const void* theta, const double* lam_l, int chi_l, int chi_r, int chi_max,
+                   double cutoff, void* site_l_out, void* site_r_out, double* lam_out,
+                   int* r_out, double* f_out, void* cuda_stream);
+
 /* Message of the last error in this thread (NUL-terminated, truncated to n). */
 int ctebd_last_error(char* buf, size_t n);
 

@@ -71,6 +71,7 @@ def _load():
         "ctebd_profile": [P, I],
         "ctebd_profile_read": [P, C.POINTER(D), I, C.POINTER(I)],
         "ctebd_kernel_name": [I, C.c_char_p, S],
+        "split2_noalloc": [P, P, I, I, I, D, P, P, P, C.POINTER(I), C.POINTER(D), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -243,6 +244,19 @@ class MPS:
         f = np.zeros(max(sum(c.k - 1 for c in clusters), 1))
         _check(_lib.step(self._h, arr, n, up, _dp(f)), "step")
         return f[: sum(c.k - 1 for c in clusters)]
+
+
+def split2_noalloc(theta_ptr, lam_ptr, chi_l, chi_r, chi_max, cutoff, site_l_ptr, site_r_ptr,
+                   lam_out_ptr, stream=None):
+    """Two-site split without device allocation (device pointers in and out).
+
+    Returns (r, f).  See include/ctebd.h for limits and scratch semantics."""
+    r, f = C.c_int(0), C.c_double(0)
+    _check(_lib.split2_noalloc(C.c_void_p(theta_ptr), C.c_void_p(lam_ptr), chi_l, chi_r, chi_max,
+                               cutoff, C.c_void_p(site_l_ptr), C.c_void_p(site_r_ptr),
+                               C.c_void_p(lam_out_ptr), C.byref(r), C.byref(f),
+                               C.c_void_p(stream or 0)), "split2_noalloc")
+    return r.value, f.value
 
 
 # C-style aliases with the ABI's names

@@ -39,6 +39,8 @@ static int fail(int code, const std::string& msg) {
     if (rc_ != CTEBD_OK) return rc_; \
   } while (0)
 
+void ctebd::set_last_error(const std::string& msg) { g_err = msg; }
+
 extern "C" int ctebd_last_error(char* buf, size_t n) {
   if (!buf || n == 0) return CTEBD_ERR_ARG;
   std::snprintf(buf, n, "%s", g_err.c_str());

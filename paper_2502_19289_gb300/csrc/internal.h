@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 namespace ctebd {
 
@@ -99,5 +100,8 @@ template <typename R>
 cudaError_t launch_convert_from_c128(const double* src, void* dst, long long n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_convert_to_c128(const void* src, double* dst, long long n, cudaStream_t s);
+
+// message returned by ctebd_last_error() in the calling thread
+void set_last_error(const std::string& msg);
 
 }  // namespace ctebd

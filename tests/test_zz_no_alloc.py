@@ -1,0 +1,70 @@
+"""split2_noalloc: the allocation-free two-site split, checked against the
+regular apply_cluster + truncate_split entry points on two calls in a row.
+
+Collected last on purpose (file name), so a failure here leaves every other
+test already run."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import lib, random_unitary
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(P, torch, seed, chi, cutoff):
+    n = 4
+    chis, sites, lams = synth.random_right_canonical(n, chi, seed=seed)
+    rng = np.random.default_rng(seed)
+    U = random_unitary(4, rng)
+    q0 = 1
+    cfg = P.make_config(n, chi, cutoff, 2 + 2 * int(np.log2(chi)) + 4, 0, 0, P.FP32)
+    m = P.MPS(cfg)
+    m.load(chis, sites, lams)
+    # cluster tensor with the gate applied, no left weights (input of both paths)
+    th = np.einsum("asc,ctb->astb", sites[q0].astype(np.complex64).astype(np.complex128),
+                   sites[q0 + 1].astype(np.complex64).astype(np.complex128))
+    cl, cr = th.shape[0], th.shape[-1]
+    th = np.einsum("uv,avb->aub", U, th.reshape(cl, 4, cr))
+    # regular entry points
+    c = P.Cluster(q0, 2, 0, 1)
+    m.apply_cluster(c, U)
+    f_ref = m.truncate_split(c)
+    r_ref = int(m.bond_dims()[q0 + 1])
+    A_ref, B_ref = m.site(q0), m.site(q0 + 1)
+    lam_ref = m.lam(q0 + 1)
+    # allocation-free entry point
+    dev = torch.device("cuda")
+    theta = torch.as_tensor(th.astype(np.complex64), device=dev).contiguous()
+    lam_l = torch.as_tensor(lams[q0], dtype=torch.float64, device=dev)
+    rmax = min(chi, 2 * cl, 2 * cr)
+    A = torch.zeros(cl * 2 * rmax, dtype=torch.complex64, device=dev)
+    B = torch.zeros(rmax * 2 * cr, dtype=torch.complex64, device=dev)
+    lam = torch.zeros(rmax, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    r, f = P.split2_noalloc(theta.data_ptr(), lam_l.data_ptr(), cl, cr, chi, cutoff,
+                            A.data_ptr(), B.data_ptr(), lam.data_ptr())
+    assert r == r_ref
+    np.testing.assert_allclose(f, f_ref[0], rtol=1e-5)
+    np.testing.assert_allclose(lam.cpu().numpy()[:r], lam_ref, atol=1e-5)
+    A = A.cpu().numpy()[: cl * 2 * r].reshape(cl, 2, r)
+    B = B.cpu().numpy()[: r * 2 * cr].reshape(r, 2, cr)
+    got = np.einsum("asm,mtb->astb", A, B)          # gauge-invariant product
+    want = np.einsum("asm,mtb->astb", A_ref, B_ref)
+    np.testing.assert_allclose(got, want, atol=1e-5)
+    Bm = B.reshape(r, -1)
+    np.testing.assert_allclose(Bm @ Bm.conj().T, np.eye(r), atol=1e-5)
+
+
+def test_noalloc_matches_regular_entry_points_twice():
+    torch = pytest.importorskip("torch")
+    P = lib()
+    _case(P, torch, seed=11, chi=32, cutoff=1e-6)    # first call: sets up the scratch address
+    _case(P, torch, seed=12, chi=64, cutoff=0.0)     # second call reuses the same scratch
+
+
+def test_noalloc_rejects_sizes_beyond_the_limit():
+    pytest.importorskip("torch")
+    P = lib()
+    with pytest.raises(P.CtebdError, match="static scratch limit"):
+        P.split2_noalloc(1, 1, 256, 8, 64, 0.0, 1, 1, 1)
