@@ -88,12 +88,18 @@ typedef struct {
   double param;
 } ctebd_gate;
 
-/* One entanglement cluster: qubits q0..q0+k-1 (Sec. III.A). */
+/* One entanglement cluster: qubits q0..q0+k-1 (Sec. III.A).  rank_hint[j-1]
+   (j = 1..k-1) is an estimate of the rank of theta across the internal bond
+   q0+j; when sketching is enabled (FP32, sketch_oversample > 0) a positive
+   hint h with 2 (h + p) <= n sizes a randomized range finder with l = h + p
+   columns for that split, otherwise (<= 0) the split is the full eigen-solve.
+   cluster_partition sets the hints to 0. */
 typedef struct {
   int q0;
   int k;
   int layer_lo;       /* gates with layer_lo < layer <= layer_hi belong to it */
   int layer_hi;
+  int rank_hint[11];
 } ctebd_cluster;
 
 typedef struct ctebd_mps ctebd_mps;
@@ -130,6 +136,16 @@ int cluster_partition(const ctebd_gate* gates, int n_gates, int layer_start,
    written row-major 2^k x 2^k complex128 (q0 is the MSB).  Host function.
    Errors: ARG (a gate straddles the window). */
 int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c, double* U);
+
+/* Eq. 9 (virtual-MPS bond estimate) as a rank bound for the splits of
+   cluster c: out[j-1] = min(chi[q0+j] * prod osr(g), chi[q0] 2^j,
+   2^(k-j) chi[q0+k]) where the product runs over the cluster's gates whose
+   qubits straddle bond q0+j and osr is the gate's operator-Schmidt rank
+   across the cut (2 for controlled gates, 4 for SWAP, sqrt(SWAP) and
+   three-qubit gates).  chi: current bond dimensions (n+1).  Host function.
+   Errors: ARG. */
+int cluster_rank_bounds(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c,
+                        const int* chi, int* out);
 
 /* One-qubit gate on a qubit outside every cluster (applied to its site's
    physical index; the paper is silent on such qubits).  u: 2x2 complex128
@@ -188,10 +204,15 @@ int mps_load(ctebd_mps* mps, const int* chi, const double* const* sites,
 int mps_load_device(ctebd_mps* mps, const int* chi, const void* const* sites,
                     const double* const* lambdas);
 
-/* Per-split log of the last step() / truncate_split: rows of 8 doubles
-   (q0, k, bond, m, n, r, f, W).  *n_rows receives the row count; up to cap
-   rows are written. */
+/* Per-split log of the last step() / truncate_split: rows of 12 doubles
+   (q0, k, bond, m, n, r, f, W, sketched, eigen-dimension, rank before the
+   chi_max cap, rank hint).  *n_rows receives the row count; up to cap rows
+   are written. */
 int mps_split_log(const ctebd_mps* mps, double* rows, int cap, int* n_rows);
+
+/* Sketched splits attempted and fallen back to the full split (the tail
+   check failed) since mps_create: out[0], out[1]. */
+int mps_sketch_stats(const ctebd_mps* mps, double* out);
 
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0

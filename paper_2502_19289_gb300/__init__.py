@@ -37,7 +37,8 @@ class Gate(C.Structure):
 
 
 class Cluster(C.Structure):
-    _fields_ = [("q0", C.c_int), ("k", C.c_int), ("layer_lo", C.c_int), ("layer_hi", C.c_int)]
+    _fields_ = [("q0", C.c_int), ("k", C.c_int), ("layer_lo", C.c_int), ("layer_hi", C.c_int),
+                ("rank_hint", C.c_int * 11)]
 
 
 def _load():
@@ -67,6 +68,8 @@ def _load():
         "mps_load": [P, C.POINTER(I), C.POINTER(C.POINTER(D)), C.POINTER(C.POINTER(D))],
         "mps_load_device": [P, C.POINTER(I), C.POINTER(P), C.POINTER(P)],
         "mps_split_log": [P, C.POINTER(D), I, C.POINTER(I)],
+        "mps_sketch_stats": [P, C.POINTER(D)],
+        "cluster_rank_bounds": [C.POINTER(Gate), I, C.POINTER(Cluster), C.POINTER(I), C.POINTER(I)],
         "ctebd_last_error": [C.c_char_p, S],
         "ctebd_profile": [P, I],
         "ctebd_profile_read": [P, C.POINTER(D), I, C.POINTER(I)],
@@ -104,7 +107,7 @@ def _ip(a: np.ndarray):
 
 
 def make_config(n_qubits, chi_max, cutoff, q_max, l_max=0, k_max=0, precision=FP32,
-                sketch_oversample=16, power_iters=1, use_rank_model=0, seed=1234) -> Config:
+                sketch_oversample=0, power_iters=1, use_rank_model=0, seed=1234) -> Config:
     return Config(n_qubits, chi_max, cutoff, q_max, l_max, k_max, precision,
                   sketch_oversample, power_iters, use_rank_model, seed)
 
@@ -136,6 +139,15 @@ def cluster_partition(gates, n_gates, layer_start, chi, cfg: Config):
     _check(_lib.cluster_partition(gates, n_gates, layer_start, _ip(chi), C.byref(cfg), out, cap,
                                   C.byref(n_out), C.byref(stop)), "cluster_partition")
     return [out[i] for i in range(n_out.value)], stop.value
+
+
+def cluster_rank_bounds(gates, n_gates, cl: Cluster, chi) -> np.ndarray:
+    """Eq. 9 rank bound per internal bond of the cluster (left to right)."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    out = np.zeros(max(cl.k - 1, 1), dtype=np.int32)
+    _check(_lib.cluster_rank_bounds(gates, n_gates, C.byref(cl), _ip(chi), _ip(out)),
+           "cluster_rank_bounds")
+    return out[: cl.k - 1]
 
 
 def cluster_unitary(gates, n_gates, cl: Cluster) -> np.ndarray:
@@ -213,9 +225,14 @@ class MPS:
     def split_log(self) -> np.ndarray:
         n = C.c_int(0)
         _check(_lib.mps_split_log(self._h, None, 0, C.byref(n)), "mps_split_log")
-        rows = np.zeros(8 * max(n.value, 1))
+        rows = np.zeros(12 * max(n.value, 1))
         _check(_lib.mps_split_log(self._h, _dp(rows), n.value, C.byref(n)), "mps_split_log")
-        return rows[: 8 * n.value].reshape(-1, 8)
+        return rows[: 12 * n.value].reshape(-1, 12)
+
+    def sketch_stats(self):
+        out = np.zeros(2)
+        _check(_lib.mps_sketch_stats(self._h, _dp(out)), "mps_sketch_stats")
+        return int(out[0]), int(out[1])
 
     # --- the cluster update ----------------------------------------------
     def apply_1q(self, q: int, u: np.ndarray):
@@ -293,24 +310,31 @@ class Circuit:
         self.n_layers = assign_layers(self.gates, self.n_gates, n_qubits)
 
 
-def run_iteration(mps: MPS, circ: Circuit, start: int):
+def run_iteration(mps: MPS, circ: Circuit, start: int, hint_fn=None):
     """One cluster-TEBD iteration (Sec. III.A) from layer ``start``.
 
-    Returns (clusters, stop layer, per-split fidelities)."""
+    With sketching enabled (FP32, sketch_oversample > 0) each cluster gets
+    rank hints: ``hint_fn(cluster, chi)`` if given (the learned predictor),
+    else the Eq. 9 bound.  Returns (clusters, stop layer, per-split f)."""
     chi = mps.bond_dims()
     clusters, stop = cluster_partition(circ.gates, circ.n_gates, start, chi, mps.cfg)
+    if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32:
+        for c in clusters:
+            hint = hint_fn(c, chi) if hint_fn else cluster_rank_bounds(circ.gates, circ.n_gates, c, chi)
+            for j, h in enumerate(hint[:11]):
+                c.rank_hint[j] = int(h)
     mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)
     Us = [cluster_unitary(circ.gates, circ.n_gates, c) for c in clusters]
     f = mps.step(clusters, Us) if clusters else np.zeros(0)
     return clusters, stop, f
 
 
-def simulate(circ: Circuit, cfg: Config, stream=None, callback=None) -> MPS:
+def simulate(circ: Circuit, cfg: Config, stream=None, callback=None, hint_fn=None) -> MPS:
     """Cluster-TEBD from |0...0> over the whole circuit (Sec. III.A loop)."""
     mps = MPS(cfg, stream)
     start = 0
     while start < circ.n_layers:
-        clusters, stop, f = run_iteration(mps, circ, start)
+        clusters, stop, f = run_iteration(mps, circ, start, hint_fn)
         if callback:
             callback(start, stop, clusters, f)
         start = stop

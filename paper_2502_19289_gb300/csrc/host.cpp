@@ -174,6 +174,7 @@ extern "C" int cluster_partition(const ctebd_gate* gates, int n_gates, int layer
       out[nc].k = b - b1 + 1;
       out[nc].layer_lo = layer_start;
       out[nc].layer_hi = stop;
+      for (int j = 0; j < 11; j++) out[nc].rank_hint[j] = 0;
     }
     ++nc;
   }
@@ -294,9 +295,18 @@ struct Work {
   size_t eigElems = 0, jElems = 0;
   double* rho = nullptr;
   int* perm = nullptr;
-  double* res = nullptr;
+  double* res = nullptr; // [0..7] select results, [8] ||M||^2, [12..15] int status
+  // sketched split (FP32, sketch enabled): Y and Q (m x l), B^H and Q_B (n x l),
+  // FP64 Cholesky work (2 l^2 complex128) and the triangular factor X (l x l)
+  void* Ys = nullptr;
+  void* Qs = nullptr;
+  void* Bs = nullptr;
+  void* QB = nullptr;
+  void* CW = nullptr;
+  void* X = nullptr;
   size_t nmax = 0;
   int rdim = 0;          // current right dimension during splitting
+  int hint[12] = {0};    // rank hints per internal bond (<= 0: none)
   bool owned = false;    // buffers allocated individually (apply_cluster path)
 };
 
@@ -307,11 +317,11 @@ struct Work {
 // ---------------------------------------------------------------------------
 enum KernelKind {
   KK_GEMM_MERGE, KK_GEMM_U, KK_GEMM_GRAM, KK_GEMM_PROJ, KK_EIG_INIT, KK_EIG_INNER, KK_EIG_APPLY,
-  KK_COLNORM, KK_SELECT, KK_GATHER, KK_ONEQ, KK_AMP, KK_COUNT
+  KK_COLNORM, KK_SELECT, KK_GATHER, KK_ONEQ, KK_AMP, KK_GEMM_SKETCH, KK_CHOL, KK_COUNT
 };
 static const char* kKindNames[KK_COUNT] = {
   "gemm_merge", "gemm_apply_u", "gemm_gram", "gemm_project", "eig_init", "eig_inner", "eig_apply",
-  "colnorm", "select", "gather", "apply_1q", "amplitude"};
+  "colnorm", "select", "gather", "apply_1q", "amplitude", "gemm_sketch", "cholqr"};
 
 struct Prof {
   bool on = false;
@@ -380,6 +390,9 @@ struct ctebd_mps {
   int lam_cap = 0;
   double logF = 0;
   std::vector<double> splitlog;
+  std::vector<double> splitlog2;   // per split: sketched, eigen-dim, rank before cap, hint
+  double sk_stats[2] = {0, 0};     // sketched splits attempted, fallen back
+  uint64_t nstep = 0;
   void* arena = nullptr;
   size_t arena_cap = 0;
   Staging stage;
@@ -434,7 +447,7 @@ extern "C" int mps_create(const ctebd_config* cfg, void* cuda_stream, ctebd_mps*
   m->lam.assign(m->n + 1, nullptr);
   int rc = m->stage.init(8 << 20, m->stream);
   if (rc) { mps_destroy(m); return rc; }
-  if (cudaMallocHost(&m->h_res, 8 * sizeof(double) * 4096) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "pinned"); }
+  if (cudaMallocHost(&m->h_res, 16 * sizeof(double) * 4096) != cudaSuccess) { mps_destroy(m); return fail(CTEBD_ERR_OOM, "pinned"); }
   m->h_res_cap = 4096;
   std::vector<double> one(1, 1.0);
   for (int b = 0; b <= m->n; b++) {
@@ -458,12 +471,15 @@ extern "C" int mps_create(const ctebd_config* cfg, void* cuda_stream, ctebd_mps*
   return CTEBD_OK;
 }
 
+static std::vector<std::pair<void**, size_t>> work_buffers(const ctebd_mps* m, Work& w);
+
 extern "C" int mps_destroy(ctebd_mps* m) {
   if (!m) return CTEBD_ERR_ARG;
   if (m->stream) cudaStreamSynchronize(m->stream);
   for (auto& kv : m->pending) {
     Work& w = kv.second;
-    if (w.owned) { cudaFree(w.bufA); cudaFree(w.bufB); cudaFree(w.G); cudaFree(w.V); cudaFree(w.W); cudaFree(w.J); cudaFree(w.rho); cudaFree(w.perm); cudaFree(w.res); }
+    if (w.owned)
+      for (auto& pb : work_buffers(m, w)) if (*pb.first) cudaFree(*pb.first);
   }
   for (void* p : m->site) if (p) cudaFree(p);
   for (double* p : m->lam) if (p) cudaFree(p);
@@ -522,13 +538,29 @@ static void work_sizes(const ctebd_mps* m, Work& w) {
   w.jElems = std::max(npad * 2 * JB, ((size_t)1 << k) * ((size_t)1 << k));
 }
 
+// every device buffer of a work item: (pointer slot, bytes)
+static std::vector<std::pair<void**, size_t>> work_buffers(const ctebd_mps* m, Work& w) {
+  std::vector<std::pair<void**, size_t>> b = {
+      {&w.bufA, w.bufElems * m->esz}, {&w.bufB, w.bufElems * m->esz}, {&w.G, w.eigElems * m->esz},
+      {&w.V, w.eigElems * m->esz},    {&w.W, w.eigElems * m->esz},    {&w.J, w.jElems * m->esz},
+      {(void**)&w.rho, w.nmax * 8},   {(void**)&w.perm, w.nmax * 4},  {(void**)&w.res, 256}};
+  if (!m->fp64 && m->cfg.sketch_oversample > 0) {
+    b.push_back({&w.Ys, w.bufElems / 2 * m->esz});
+    b.push_back({&w.Qs, w.bufElems / 2 * m->esz});
+    b.push_back({&w.Bs, w.eigElems / 2 * m->esz});
+    b.push_back({&w.QB, w.eigElems / 2 * m->esz});
+    b.push_back({&w.CW, w.eigElems * 16});
+    b.push_back({&w.X, w.eigElems / 4 * m->esz});
+  }
+  return b;
+}
+
 static int carve_work(ctebd_mps* m, std::vector<Work>& ws) {
   size_t total = 0;
-  auto al = [](size_t b) { return round_up(b, 256); };
+  auto al = [](size_t b) { return round_up(std::max<size_t>(b, 16), 256); };
   for (auto& w : ws) {
     work_sizes(m, w);
-    total += 2 * al(w.bufElems * m->esz) + 3 * al(w.eigElems * m->esz) + al(w.jElems * m->esz) +
-             al(w.nmax * 8) + al(w.nmax * 4) + al(64);
+    for (auto& pb : work_buffers(m, w)) total += al(pb.second);
   }
   if (total > m->arena_cap) {
     CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -543,43 +575,27 @@ static int carve_work(ctebd_mps* m, std::vector<Work>& ws) {
     m->arena_cap = want;
   }
   unsigned char* p = (unsigned char*)m->arena;
-  for (auto& w : ws) {
-    w.bufA = p; p += al(w.bufElems * m->esz);
-    w.bufB = p; p += al(w.bufElems * m->esz);
-    w.G = p; p += al(w.eigElems * m->esz);
-    w.V = p; p += al(w.eigElems * m->esz);
-    w.W = p; p += al(w.eigElems * m->esz);
-    w.J = p; p += al(w.jElems * m->esz);
-    w.rho = (double*)p; p += al(w.nmax * 8);
-    w.perm = (int*)p; p += al(w.nmax * 4);
-    w.res = (double*)p; p += al(64);
-  }
+  for (auto& w : ws)
+    for (auto& pb : work_buffers(m, w)) {
+      *pb.first = p;
+      p += al(pb.second);
+    }
   return CTEBD_OK;
 }
 
 static int alloc_owned(ctebd_mps* m, Work& w) {
   work_sizes(m, w);
-  auto A = [&](void** p, size_t b) -> int {
-    if (cudaMallocAsync(p, std::max<size_t>(b, 16), m->stream) != cudaSuccess) return fail(CTEBD_ERR_OOM, "work buffer");
-    return CTEBD_OK;
-  };
-  TRY(A(&w.bufA, w.bufElems * m->esz));
-  TRY(A(&w.bufB, w.bufElems * m->esz));
-  TRY(A(&w.G, w.eigElems * m->esz));
-  TRY(A(&w.V, w.eigElems * m->esz));
-  TRY(A(&w.W, w.eigElems * m->esz));
-  TRY(A(&w.J, w.jElems * m->esz));
-  TRY(A((void**)&w.rho, w.nmax * 8));
-  TRY(A((void**)&w.perm, w.nmax * 4));
-  TRY(A((void**)&w.res, 64));
+  for (auto& pb : work_buffers(m, w))
+    if (cudaMallocAsync(pb.first, std::max<size_t>(pb.second, 16), m->stream) != cudaSuccess)
+      return fail(CTEBD_ERR_OOM, "work buffer");
   w.owned = true;
   return CTEBD_OK;
 }
 
 static void free_owned(ctebd_mps* m, Work& w) {
   if (!w.owned) return;
-  for (void* p : {w.bufA, w.bufB, w.G, w.V, w.W, w.J, (void*)w.rho, (void*)w.perm, (void*)w.res})
-    if (p) cudaFreeAsync(p, m->stream);
+  for (auto& pb : work_buffers(m, w))
+    if (*pb.first) cudaFreeAsync(*pb.first, m->stream);
   w.owned = false;
 }
 
@@ -640,26 +656,38 @@ static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<co
 }
 
 // ---------------------------------------------------------------------------
-// Split pieces (one level = one bond per active cluster)
+// Split pieces (one level = one bond per active cluster).  A problem's
+// eigen-dimension ne is its column count n (full split) or the sketch size l
+// (sketched split: Rayleigh-Ritz on the range of M^H Q).
 // ---------------------------------------------------------------------------
 struct Level {
   std::vector<int> act;                        // indices into ws
-  std::vector<int> mm, nn, npad, nbv, shift;   // per active problem
+  std::vector<int> mm, nn, npad, shift;        // M-bar rows / cols, padded cols, lambda shift
+  std::vector<int> ne, nepad, nbv, vld;        // eigen-dimension, padded, blocks, ld of V
+  std::vector<char> sk;                        // sketched
 };
 
-// G = Z^H diag(lambda_L^2) Z for Z = bufA (Mbar) or bufB (Mbar V)
+static void level_set_full(Level& L, int a, int JB) {
+  L.sk[a] = 0;
+  L.ne[a] = L.nn[a];
+  L.nepad[a] = L.npad[a];
+  L.nbv[a] = L.npad[a] / JB;
+  L.vld[a] = L.npad[a];
+}
+
+// G = Z^H diag(lambda_L^2) Z over the m rows of Z (ne columns, row-major)
 static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
-                      bool from_rotated) {
+                      const std::vector<const void*>& Z) {
   std::vector<GemmProb> probs;
-  for (int a : sel) {
+  for (size_t i = 0; i < sel.size(); i++) {
+    const int a = sel[i];
     Work& w = ws[L.act[a]];
-    CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)L.npad[a] * L.npad[a] * m->esz, m->stream));
+    CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)L.nepad[a] * L.nepad[a] * m->esz, m->stream));
     GemmProb p{};
-    const void* Z = from_rotated ? w.bufB : w.bufA;
-    p.M = L.nn[a]; p.N = L.nn[a]; p.K = L.mm[a]; p.batch = 1;
-    p.A = Z; p.lda = L.nn[a]; p.opA = 1;
-    p.B = Z; p.ldb = L.nn[a]; p.opB = 0;
-    p.C = w.G; p.ldc = L.npad[a];
+    p.M = L.ne[a]; p.N = L.ne[a]; p.K = L.mm[a]; p.batch = 1;
+    p.A = Z[i]; p.lda = L.ne[a]; p.opA = 1;
+    p.B = Z[i]; p.ldb = L.ne[a]; p.opB = 0;
+    p.C = w.G; p.ldc = L.nepad[a];
     p.kw = m->lam[w.q0];
     p.kw_shift = L.shift[a];
     p.alpha = 1.0;
@@ -669,7 +697,7 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 }
 
 // Batched block-Jacobi on every G of the selection; rotations accumulate
-// into acc[a] (set to identity first).  floor_factor scales the absolute
+// into acc[i] (set to identity first).  floor_factor scales the absolute
 // rotation floor eps * trace(G): 1 for a Gram computed from Mbar (absolute
 // rounding), ~0 for a Gram of already rotated columns (relative accuracy).
 static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
@@ -686,11 +714,11 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     const int a = sel[i];
     Work& w = ws[L.act[a]];
     eps[i].G = w.G; eps[i].V = acc[i]; eps[i].J = w.J;
-    eps[i].npad = L.npad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
+    eps[i].npad = L.nepad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
     eps[i].off = d_off + 2 * i;
     eps[i].scale = d_off + 2 * na + i;
     eps[i].floor_factor = floor_factor;
-    max_npad = std::max(max_npad, L.npad[a]);
+    max_npad = std::max(max_npad, L.nepad[a]);
     max_nb = std::max(max_nb, L.nbv[a]);
   }
   const EigProb* dep;
@@ -711,7 +739,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       for (int i = 0; i < na; i++) {
         const int a = sel[i];
         if (!eps[i].active || t >= L.nbv[a] - 1) continue;
-        const double h = L.nbv[a] / 2, np2 = (double)L.npad[a] * L.npad[a];
+        const double h = L.nbv[a] / 2, np2 = (double)L.nepad[a] * L.nepad[a];
         bin += 2 * h * D * D * m->esz;                           // read blocks, write J
         fap += 8.0 * (2 * h * (h + 1) / 2 + h * h) * D * D * D;  // J^H G J (upper tiles), V J
         bap += (4 * np2 + h * D * D) * m->esz;                   // G, V read+write, J read
@@ -744,7 +772,8 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   return CTEBD_OK;
 }
 
-// Rfull = Mbar V (bufB), rho = weighted column norms, then truncation select
+// Rfull = Mbar V (bufB, m x ne), rho = weighted column norms, truncation
+// select (with the total weight ||M||^2 for sketched problems); results to host
 static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level& L,
                                 const std::vector<int>& sel) {
   const bool f64 = m->fp64;
@@ -756,13 +785,13 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
   for (int a : sel) {
     Work& w = ws[L.act[a]];
     GemmProb p{};
-    p.M = L.mm[a]; p.N = L.nn[a]; p.K = L.nn[a]; p.batch = 1;
+    p.M = L.mm[a]; p.N = L.ne[a]; p.K = L.nn[a]; p.batch = 1;
     p.A = w.bufA; p.lda = L.nn[a]; p.opA = 0;
-    p.B = w.V; p.ldb = L.npad[a]; p.opB = 0;
-    p.C = w.bufB; p.ldc = L.nn[a]; p.alpha = 1.0;
+    p.B = w.V; p.ldb = L.vld[a]; p.opB = 0;
+    p.C = w.bufB; p.ldc = L.ne[a]; p.alpha = 1.0;
     probs.push_back(p);
-    CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * L.nn[a], m->stream));
-    max_n = std::max(max_n, L.nn[a]);
+    CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * L.ne[a], m->stream));
+    max_n = std::max(max_n, L.ne[a]);
     max_m = std::max(max_m, L.mm[a]);
   }
   TRY(run_gemms(m, probs, KK_GEMM_PROJ));
@@ -776,7 +805,7 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
       const int a = sel[i];
       Work& w = ws[L.act[a]];
       R[i] = w.bufB; Lm[i] = m->lam[w.q0]; rho[i] = w.rho;
-      mm[i] = L.mm[a]; nn[i] = L.nn[a]; sh[i] = L.shift[a];
+      mm[i] = L.mm[a]; nn[i] = L.ne[a]; sh[i] = L.shift[a];
       by += (double)mm[i] * nn[i] * m->esz;
     }
     const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
@@ -794,9 +823,10 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
     Work& w = ws[L.act[a]];
-    sp[i].rho = w.rho; sp[i].n = L.nn[a]; sp[i].perm = w.perm;
+    sp[i].rho = w.rho; sp[i].n = L.ne[a]; sp[i].perm = w.perm;
     sp[i].lam_out = m->lam[w.q0 + L.shift[a]]; sp[i].res = w.res;
-    if (L.nn[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
+    sp[i].W_ext = L.sk[a] ? w.res + 8 : nullptr;
+    if (L.ne[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
   }
   const SelProb* dsp;
   TRY(m->stage.push(sp.data(), na, &dsp));
@@ -804,19 +834,230 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
     ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
     CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, floor_rel * floor_rel, m->stream));
   }
-  // results land at the level-local index a (h_res[8 a .. 8 a + 7])
+  // results land at the level-local index a (h_res[16 a .. 16 a + 15])
   if (L.act.size() > m->h_res_cap) return fail(CTEBD_ERR_ARG, "too many clusters");
   for (int a : sel)
-    CUDA_TRY(cudaMemcpyAsync(m->h_res + 8 * a, ws[L.act[a]].res, 8 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(m->h_res + 16 * a, ws[L.act[a]].res, 16 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   m->stage.reset();
   return CTEBD_OK;
 }
 
+// CholeskyQR passes on the columns of X (rows x l, ld l) -> orthonormal Q in
+// out; shifted first pass (shifted CholeskyQR3) so the Cholesky never breaks
+// down on rank-deficient or ill-conditioned sketches.
+static int level_cholqr(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
+                        const std::vector<int>& rows, const std::vector<int>& lcols,
+                        std::vector<void*>& X, std::vector<void*>& tmp) {
+  const int na = (int)sel.size();
+  for (int pass = 0; pass < 3; pass++) {
+    std::vector<GemmProb> gram, mul;
+    std::vector<CholProb> cp(na);
+    for (int i = 0; i < na; i++) {
+      Work& w = ws[L.act[sel[i]]];
+      const int l = lcols[i];
+      CUDA_TRY(cudaMemsetAsync(w.G, 0, (size_t)l * l * m->esz, m->stream));
+      GemmProb g{};
+      g.M = l; g.N = l; g.K = rows[i]; g.batch = 1;
+      g.A = X[i]; g.lda = l; g.opA = 1; g.B = X[i]; g.ldb = l; g.opB = 0;
+      g.C = w.G; g.ldc = l; g.alpha = 1.0;
+      gram.push_back(g);
+      cp[i].G = w.G; cp[i].ldg = l; cp[i].l = l;
+      cp[i].shift_rel = pass == 0 ? 1e-5 : 0.0;
+      cp[i].dead_rel = pass == 0 ? 0.0 : 2e-6;
+      cp[i].dead = w.perm;   // perm is free until the select
+      cp[i].X = w.X; cp[i].ldx = l;
+      cp[i].work = (double2*)w.CW;
+      cp[i].status = (int*)(w.res + 12);
+      GemmProb q{};
+      q.M = rows[i]; q.N = l; q.K = l; q.batch = 1;
+      q.A = X[i]; q.lda = l; q.opA = 0; q.B = w.X; q.ldb = l; q.opB = 0;
+      q.C = tmp[i]; q.ldc = l; q.alpha = 1.0;
+      mul.push_back(q);
+    }
+    TRY(run_gemms(m, gram, KK_GEMM_GRAM));
+    const CholProb* dcp;
+    TRY(m->stage.push(cp.data(), cp.size(), &dcp));
+    {
+      ProfScope ps(m->prof, m->stream, KK_CHOL, 0, 0);
+      CUDA_TRY(launch_chol_inv(dcp, na, m->stream));
+    }
+    TRY(run_gemms(m, mul, KK_GEMM_PROJ));
+    std::swap(X, tmp);
+  }
+  std::vector<int> st(na);
+  for (int i = 0; i < na; i++)
+    CUDA_TRY(cudaMemcpyAsync(&st[i], ws[L.act[sel[i]]].res + 12, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->stage.reset();
+  for (int i = 0; i < na; i++)
+    if (st[i] != 0) return fail(CTEBD_ERR_NUMERIC, "CholeskyQR: non-finite sketch");
+  return CTEBD_OK;
+}
+
+// Sketched basis (spec range finder): Y = M Omega (power iterations
+// Y <- M M^H Y), Q = CholQR(Y), B^H = M^H Q, Q_B = CholQR(B^H); then
+// Z = Mbar Q_B (bufB) for the Rayleigh-Ritz Gram.  M = diag(lambda_L) Mbar.
+static int level_sketch(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
+                        uint64_t step_key) {
+  const int na = (int)sel.size();
+  if (na == 0) return CTEBD_OK;
+  auto rowscale = [&](const std::vector<void*>& Xs, const std::vector<int>& rows) -> int {
+    std::vector<RowScaleProb> rp(na);
+    long long mx = 0;
+    for (int i = 0; i < na; i++) {
+      const int a = sel[i];
+      rp[i].X = Xs[i]; rp[i].rows = rows[i]; rp[i].cols = L.ne[a]; rp[i].ld = L.ne[a];
+      rp[i].lam = m->lam[ws[L.act[a]].q0]; rp[i].shift = L.shift[a];
+      mx = std::max(mx, (long long)rows[i] * L.ne[a]);
+    }
+    const RowScaleProb* drp;
+    TRY(m->stage.push(rp.data(), rp.size(), &drp));
+    CUDA_TRY(launch_rowscale(drp, na, mx, m->stream));
+    return CTEBD_OK;
+  };
+  std::vector<int> mrows(na), nrows(na), ls(na);
+  std::vector<void*> Y(na), Qv(na), Bv(na), QBv(na);
+  for (int i = 0; i < na; i++) {
+    const int a = sel[i];
+    Work& w = ws[L.act[a]];
+    mrows[i] = L.mm[a]; nrows[i] = L.nn[a]; ls[i] = L.ne[a];
+    Y[i] = w.Ys; Qv[i] = w.Qs; Bv[i] = w.Bs; QBv[i] = w.QB;
+    // Omega (n x l) in QB, counter-based: key = seed, stream = (step, cluster, bond)
+    const uint64_t stream = (step_key << 24) ^ ((uint64_t)w.q0 << 8) ^ (uint64_t)L.shift[a];
+    CUDA_TRY(launch_gauss(w.QB, (long long)L.nn[a] * L.ne[a], m->cfg.seed, stream, m->stream));
+  }
+  auto gemm_MY = [&](const std::vector<void*>& B, const std::vector<void*>& C) -> int {  // C = Mbar B
+    std::vector<GemmProb> pr;
+    for (int i = 0; i < na; i++) {
+      const int a = sel[i];
+      GemmProb p{};
+      p.M = L.mm[a]; p.N = L.ne[a]; p.K = L.nn[a]; p.batch = 1;
+      p.A = ws[L.act[a]].bufA; p.lda = L.nn[a]; p.opA = 0;
+      p.B = B[i]; p.ldb = L.ne[a]; p.opB = 0; p.C = C[i]; p.ldc = L.ne[a]; p.alpha = 1.0;
+      pr.push_back(p);
+    }
+    return run_gemms(m, pr, KK_GEMM_SKETCH);
+  };
+  auto gemm_MhY = [&](const std::vector<void*>& B, const std::vector<void*>& C) -> int {  // C = Mbar^H D B
+    std::vector<GemmProb> pr;
+    for (int i = 0; i < na; i++) {
+      const int a = sel[i];
+      Work& w = ws[L.act[a]];
+      GemmProb p{};
+      p.M = L.nn[a]; p.N = L.ne[a]; p.K = L.mm[a]; p.batch = 1;
+      p.A = w.bufA; p.lda = L.nn[a]; p.opA = 1;
+      p.B = B[i]; p.ldb = L.ne[a]; p.opB = 0; p.C = C[i]; p.ldc = L.ne[a]; p.alpha = 1.0;
+      p.kw = m->lam[w.q0]; p.kw_shift = L.shift[a]; p.kw_pow = 1;
+      pr.push_back(p);
+    }
+    return run_gemms(m, pr, KK_GEMM_SKETCH);
+  };
+  TRY(gemm_MY(QBv, Y));                // Y = Mbar Omega
+  TRY(rowscale(Y, mrows));             // Y = M Omega
+  for (int q = 0; q < m->cfg.power_iters; q++) {
+    TRY(gemm_MhY(Y, Bv));              // Z = M^H Y
+    TRY(gemm_MY(Bv, Y));
+    TRY(rowscale(Y, mrows));           // Y = M Z
+  }
+  // level_cholqr leaves the orthonormal factor in the buffers its first vector
+  // names on return (three ping-pong passes): Q ends in Qs, Q_B in QB
+  TRY(level_cholqr(m, ws, L, sel, mrows, ls, Y, Qv));
+  TRY(gemm_MhY(Y, Bv));                // B^H = M^H Q   (n x l)
+  std::vector<void*> Bx = Bv, Btmp = QBv;
+  TRY(level_cholqr(m, ws, L, sel, nrows, ls, Bx, Btmp));
+  for (int i = 0; i < na; i++)
+    if (Bx[i] != ws[L.act[sel[i]]].QB || Y[i] != ws[L.act[sel[i]]].Qs)
+      return fail(CTEBD_ERR_STATE, "internal: CholeskyQR buffer hand-off");
+  std::vector<void*> Zb(na);
+  for (int i = 0; i < na; i++) Zb[i] = ws[L.act[sel[i]]].bufB;
+  TRY(gemm_MY(Bx, Zb));                // Z = Mbar Q_B
+  // ||M||_F^2 (FP64) for the tail check and the total weight of the select
+  std::vector<WNormProb> wp(na);
+  long long mx = 0;
+  for (int i = 0; i < na; i++) {
+    const int a = sel[i];
+    Work& w = ws[L.act[a]];
+    CUDA_TRY(cudaMemsetAsync(w.res + 8, 0, sizeof(double), m->stream));
+    wp[i].X = w.bufA; wp[i].rows = L.mm[a]; wp[i].cols = L.nn[a]; wp[i].ld = L.nn[a];
+    wp[i].lam = m->lam[w.q0]; wp[i].shift = L.shift[a]; wp[i].out = w.res + 8;
+    mx = std::max(mx, (long long)L.mm[a] * L.nn[a]);
+  }
+  const WNormProb* dwp;
+  TRY(m->stage.push(wp.data(), wp.size(), &dwp));
+  CUDA_TRY(launch_wnorm(dwp, na, mx, m->stream));
+  return CTEBD_OK;
+}
+
+// pass 1 (+ FP32 pass 2) for a selection: Gram of Z, eigen-solve, V, weights, select
+static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std::vector<int>& sel) {
+  if (sel.empty()) return CTEBD_OK;
+  const bool f64 = m->fp64;
+  std::vector<const void*> Z;
+  std::vector<void*> accV;
+  for (int a : sel) {
+    Work& w = ws[L.act[a]];
+    Z.push_back(L.sk[a] ? w.bufB : w.bufA);
+    accV.push_back(L.sk[a] ? w.W : w.V);
+  }
+  TRY(level_gram(m, ws, L, sel, Z));
+  TRY(level_eig(m, ws, L, sel, accV, 1.0));
+  // sketched problems: V = Q_B W (n x l, ld nepad) into V
+  {
+    std::vector<GemmProb> probs;
+    for (int a : sel) {
+      if (!L.sk[a]) continue;
+      Work& w = ws[L.act[a]];
+      GemmProb p{};
+      p.M = L.nn[a]; p.N = L.ne[a]; p.K = L.ne[a]; p.batch = 1;
+      p.A = w.QB; p.lda = L.ne[a]; p.opA = 0;
+      p.B = w.W; p.ldb = L.nepad[a]; p.opB = 0;
+      p.C = w.V; p.ldc = L.vld[a]; p.alpha = 1.0;
+      probs.push_back(p);
+    }
+    TRY(run_gemms(m, probs, KK_GEMM_PROJ));
+  }
+  TRY(level_project_select(m, ws, L, sel));
+  if (f64) return CTEBD_OK;
+  // pass 2 (FP32): where the cutoff or the zero floor -- not chi_max -- decided
+  // the rank, the weights of the small directions must be accurate relative to
+  // their own size: re-diagonalise the freshly computed Gram of the rotated
+  // columns Z = M V and rotate V and Z by the result.
+  std::vector<int> ref;
+  for (int a : sel) {
+    const int r = (int)m->h_res[16 * a];
+    if (r < std::min(m->cfg.chi_max, L.ne[a])) ref.push_back(a);
+  }
+  if (ref.empty()) return CTEBD_OK;
+  std::vector<const void*> Z2;
+  std::vector<void*> accW;
+  for (int a : ref) {
+    Z2.push_back(ws[L.act[a]].bufB);
+    accW.push_back(ws[L.act[a]].W);
+  }
+  TRY(level_gram(m, ws, L, ref, Z2));
+  TRY(level_eig(m, ws, L, ref, accW, 1e-12));
+  std::vector<GemmProb> probs;
+  for (int a : ref) {
+    Work& w = ws[L.act[a]];
+    GemmProb p{};
+    p.M = L.nn[a]; p.N = L.ne[a]; p.K = L.ne[a]; p.batch = 1;
+    p.A = w.V; p.lda = L.vld[a]; p.opA = 0;
+    p.B = w.W; p.ldb = L.nepad[a]; p.opB = 0;
+    p.C = w.G; p.ldc = L.vld[a]; p.alpha = 1.0;
+    probs.push_back(p);
+  }
+  TRY(run_gemms(m, probs, KK_GEMM_PROJ));
+  for (int a : ref) std::swap(ws[L.act[a]].V, ws[L.act[a]].G);
+  return level_project_select(m, ws, L, ref);
+}
+
 // k-1 splits, right to left (Fig. 2 with the truncation of Fig. 3)
-static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::vector<double>>& fs) {
+static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::vector<double>>& fs,
+                        uint64_t step_key) {
   const bool f64 = m->fp64;
   const int JB = eig_block(f64);
+  const int p_over = m->cfg.sketch_oversample;
   fs.assign(ws.size(), {});
   int kmax = 0;
   for (auto& w : ws) kmax = std::max(kmax, w.k);
@@ -825,8 +1066,9 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
     for (size_t i = 0; i < ws.size(); i++) if (ws[i].k - 1 >= lev) L.act.push_back((int)i);
     if (L.act.empty()) break;
     const int na = (int)L.act.size();
-    L.mm.resize(na); L.nn.resize(na); L.npad.resize(na); L.nbv.resize(na); L.shift.resize(na);
-    std::vector<int> all(na);
+    for (auto* v : {&L.mm, &L.nn, &L.npad, &L.shift, &L.ne, &L.nepad, &L.nbv, &L.vld}) v->resize(na);
+    L.sk.assign(na, 0);
+    std::vector<int> sk_sel, full_sel;
     for (int a = 0; a < na; a++) {
       Work& w = ws[L.act[a]];
       const int j = w.k - lev;  // bond q0 + j is split off
@@ -834,66 +1076,61 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
       L.nn[a] = 2 * w.rdim;
       L.shift[a] = j;
       L.npad[a] = (int)round_up(L.nn[a], 2 * JB);
-      L.nbv[a] = L.npad[a] / JB;
-      all[a] = a;
       if ((size_t)L.npad[a] * L.npad[a] > w.eigElems) return fail(CTEBD_ERR_ARG, "internal: eig buffer");
-    }
-    // pass 1: Schmidt-weighted Gram of Mbar, its eigenvectors V, weights rho
-    TRY(level_gram(m, ws, L, all, false));
-    std::vector<void*> accV(na);
-    for (int a = 0; a < na; a++) accV[a] = ws[L.act[a]].V;
-    TRY(level_eig(m, ws, L, all, accV, 1.0));
-    TRY(level_project_select(m, ws, L, all));
-    // pass 2 (FP32 only): where the cutoff or the zero floor -- not chi_max --
-    // decided the rank, the weights of the small directions must be accurate
-    // relative to their own size: re-diagonalise the freshly computed Gram of
-    // the rotated columns Z = M V and rotate V and Z by the result.
-    if (!f64) {
-      std::vector<int> ref;
-      for (int a = 0; a < na; a++) {
-        const int r = (int)m->h_res[8 * a];
-        if (r < std::min(m->cfg.chi_max, L.nn[a])) ref.push_back(a);
-      }
-      if (!ref.empty()) {
-        TRY(level_gram(m, ws, L, ref, true));
-        std::vector<void*> accW(ref.size());
-        for (size_t i = 0; i < ref.size(); i++) accW[i] = ws[L.act[ref[i]]].W;
-        TRY(level_eig(m, ws, L, ref, accW, 1e-12));
-        // V <- V W (into G, then swap), Rfull recomputed from the new V
-        std::vector<GemmProb> probs;
-        for (int a : ref) {
-          Work& w = ws[L.act[a]];
-          GemmProb p{};
-          p.M = L.nn[a]; p.N = L.nn[a]; p.K = L.nn[a]; p.batch = 1;
-          p.A = w.V; p.lda = L.npad[a]; p.opA = 0;
-          p.B = w.W; p.ldb = L.npad[a]; p.opB = 0;
-          p.C = w.G; p.ldc = L.npad[a]; p.alpha = 1.0;
-          probs.push_back(p);
+      level_set_full(L, a, JB);
+      // sketched split when a rank hint makes the sketch at most half the width
+      const int h = w.hint[j - 1];
+      if (!f64 && p_over > 0 && h > 0) {
+        const int l = h + p_over;
+        if (2 * l <= L.nn[a] && (size_t)L.mm[a] * l <= w.bufElems / 2) {
+          L.sk[a] = 1;
+          L.ne[a] = l;
+          L.nepad[a] = (int)round_up(l, 2 * JB);
+          L.nbv[a] = L.nepad[a] / JB;
+          L.vld[a] = L.nepad[a];
+          sk_sel.push_back(a);
+          continue;
         }
-        TRY(run_gemms(m, probs, KK_GEMM_PROJ));
-        for (int a : ref) std::swap(ws[L.act[a]].V, ws[L.act[a]].G);
-        TRY(level_project_select(m, ws, L, ref));
+      }
+      full_sel.push_back(a);
+    }
+    if (!sk_sel.empty()) {
+      TRY(level_sketch(m, ws, L, sk_sel, step_key));
+      TRY(level_solve(m, ws, L, sk_sel));
+      // tail check: weight outside the sketch must be below max(cutoff, 1e-6) W;
+      // otherwise the split falls back to the full eigen-solve
+      const double tol = std::max(m->cfg.cutoff, 1e-6);
+      for (int a : sk_sel) {
+        const double* res = m->h_res + 16 * a;
+        const double Wt = res[2], inside = res[5];
+        m->sk_stats[0] += 1;
+        if (!(Wt - inside <= tol * Wt)) {
+          m->sk_stats[1] += 1;
+          level_set_full(L, a, JB);
+          full_sel.push_back(a);
+        }
       }
     }
+    TRY(level_solve(m, ws, L, full_sel));
     // write back: new right sites, unweighted remainders
     std::vector<GatherProb> gp;
     long long maxe = 0;
     for (int a = 0; a < na; a++) {
       Work& w = ws[L.act[a]];
       const int j = w.k - lev;
-      const double* res = m->h_res + 8 * a;   // level-local index, as written by the select
+      const double* res = m->h_res + 16 * a;   // level-local index, as written by the select
       const int r = (int)res[0];
       const double f = res[1], W = res[2], kept = res[3];
       if (!(kept > 0) || !std::isfinite(W)) return fail(CTEBD_ERR_NUMERIC, "split: non-finite or zero weight");
-      if (r < 1 || r > L.nn[a] || r > m->cfg.chi_max || r > L.mm[a] * 1LL * L.nn[a])
+      if (r < 1 || r > L.ne[a] || r > m->cfg.chi_max)
         return fail(CTEBD_ERR_NUMERIC, "split: rank out of range (" + std::to_string(r) + ")");
       const int bnd = w.q0 + j;
       TRY(ensure_site(m, bnd, (size_t)r * L.nn[a]));
       GatherProb g0{};
-      g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = L.nn[a]; g0.r = r; g0.ld = L.npad[a]; g0.mode = 0;
+      g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = L.nn[a]; g0.r = r; g0.ld = L.vld[a]; g0.mode = 0;
       gp.push_back(g0);
       GatherProb g1{};
-      g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = L.mm[a]; g1.r = r; g1.ld = L.nn[a]; g1.mode = 1;
+      g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = L.mm[a]; g1.r = r; g1.ld = L.ne[a]; g1.mode = 1;
       g1.scale = 1.0 / std::sqrt(kept);
       gp.push_back(g1);
       maxe = std::max(maxe, std::max((long long)r * L.nn[a], (long long)r * L.mm[a]));
@@ -903,6 +1140,8 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
       fs[L.act[a]].push_back(f);
       const double row[8] = {(double)w.q0, (double)w.k, (double)bnd, (double)L.mm[a], (double)L.nn[a], (double)r, f, W};
       m->splitlog.insert(m->splitlog.end(), row, row + 8);
+      const double extra[4] = {(double)L.sk[a], (double)L.ne[a], res[4], (double)w.hint[j - 1]};
+      m->splitlog2.insert(m->splitlog2.end(), extra, extra + 4);
     }
     const GatherProb* dgp;
     TRY(m->stage.push(gp.data(), gp.size(), &dgp));
@@ -925,6 +1164,7 @@ static int make_work(ctebd_mps* m, const ctebd_cluster* c, Work& w) {
   if (!c || c->k < 2 || c->q0 < 0 || c->q0 + c->k > m->n) return fail(CTEBD_ERR_ARG, "cluster out of range (k >= 2 required)");
   if (c->k > 12) return fail(CTEBD_ERR_ARG, "cluster too large");
   w.q0 = c->q0; w.k = c->k; w.chiL = m->chi[c->q0]; w.chiR = m->chi[c->q0 + c->k];
+  for (int j = 0; j < 12; j++) w.hint[j] = (j < c->k - 1 && j < 11) ? c->rank_hint[j] : 0;
   const long long D = 1LL << c->k;
   const long long theta = (long long)w.chiL * D * w.chiR;
   if (theta > (1LL << 31)) return fail(CTEBD_ERR_ARG, "cluster tensor too large");
@@ -945,12 +1185,13 @@ extern "C" int step(ctebd_mps* m, const ctebd_cluster* c, int n, const double* c
     if (m->pending.count(c[i].q0)) return fail(CTEBD_ERR_STATE, "step: cluster pending from apply_cluster");
   }
   m->splitlog.clear();
+  m->splitlog2.clear();
   m->stage.reset();
   TRY(carve_work(m, ws));
   std::vector<const double*> Us(U, U + n);
   TRY(merge_apply(m, ws, Us));
   std::vector<std::vector<double>> fs;
-  TRY(split_levels(m, ws, fs));
+  TRY(split_levels(m, ws, fs, ++m->nstep));
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   if (f_out) {
     size_t o = 0;
@@ -985,7 +1226,8 @@ extern "C" int truncate_split(ctebd_mps* m, const ctebd_cluster* c, double* f_ou
   m->splitlog.clear();
   m->stage.reset();
   std::vector<std::vector<double>> fs;
-  int rc = split_levels(m, ws, fs);
+  m->splitlog2.clear();
+  int rc = split_levels(m, ws, fs, ++m->nstep);
   free_owned(m, ws[0]);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -1185,7 +1427,50 @@ extern "C" int mps_split_log(const ctebd_mps* m, double* rows, int cap, int* n_r
   if (!m || !n_rows) return fail(CTEBD_ERR_ARG, "mps_split_log: null argument");
   const int nr = (int)(m->splitlog.size() / 8);
   *n_rows = nr;
-  if (rows) std::memcpy(rows, m->splitlog.data(), sizeof(double) * 8 * std::min(nr, cap));
+  if (rows)
+    for (int i = 0; i < std::min(nr, cap); i++) {
+      std::memcpy(rows + 12 * i, m->splitlog.data() + 8 * i, sizeof(double) * 8);
+      std::memcpy(rows + 12 * i + 8, m->splitlog2.data() + 4 * i, sizeof(double) * 4);
+    }
+  return CTEBD_OK;
+}
+
+extern "C" int mps_sketch_stats(const ctebd_mps* m, double* out) {
+  if (!m || !out) return fail(CTEBD_ERR_ARG, "mps_sketch_stats: null argument");
+  out[0] = m->sk_stats[0];
+  out[1] = m->sk_stats[1];
+  return CTEBD_OK;
+}
+
+// operator-Schmidt rank of a gate across a cut between its qubits
+static int gate_osr(int kind, int n_q) {
+  if (n_q >= 3) return 4;
+  if (kind == CTEBD_SWAP || kind == CTEBD_SQSWAP) return 4;
+  return 2;
+}
+
+extern "C" int cluster_rank_bounds(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c,
+                                   const int* chi, int* out) {
+  if (!c || !chi || !out || c->k < 2 || c->k > 12 || n_gates < 0 || (n_gates && !gates))
+    return fail(CTEBD_ERR_ARG, "cluster_rank_bounds: bad args");
+  const int k = c->k, q0 = c->q0;
+  const long long cap = 1LL << 30;
+  std::vector<long long> prod(k, 1);
+  for (int j = 1; j < k; j++) prod[j] = chi[q0 + j];
+  for (int i = 0; i < n_gates; i++) {
+    const ctebd_gate& g = gates[i];
+    if (g.layer <= c->layer_lo || g.layer > c->layer_hi || g.n_q < 2) continue;
+    int lo = g.q[0], hi = g.q[0];
+    for (int t = 1; t < g.n_q; t++) { lo = std::min(lo, g.q[t]); hi = std::max(hi, g.q[t]); }
+    if (lo < q0 || hi >= q0 + k) continue;
+    for (int b = lo + 1; b <= hi; b++) prod[b - q0] = std::min(cap, prod[b - q0] * gate_osr(g.kind, g.n_q));
+  }
+  for (int j = 1; j < k; j++) {
+    long long r = prod[j];
+    r = std::min(r, std::min(cap, (long long)chi[q0] << j));
+    r = std::min(r, std::min(cap, ((long long)1 << (k - j)) * chi[q0 + k]));
+    out[j - 1] = (int)r;
+  }
   return CTEBD_OK;
 }
 

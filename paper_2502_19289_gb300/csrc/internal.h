@@ -24,6 +24,7 @@ struct GemmProb {
   const double* kw;
   int kw_shift;
   double alpha;
+  int kw_pow;   // 1: multiply by kw; otherwise by kw^2
 };
 
 // One Hermitian eigenproblem of the batched block-Jacobi solver.  G and V are
@@ -49,7 +50,41 @@ struct SelProb {
   int* perm;           // out: kept column indices, descending rho
   double* lam_out;     // out: renormalised kept spectrum (fp64)
   double* res;         // out: [0] r, [1] f, [2] W, [3] kept, [4] rank before chi_max cap
+  const double* W_ext; // optional total weight ||M||_F^2 (sketched split): the
+                       // weight outside the n directions counts as discarded
 };
+
+struct RowScaleProb {   // X[r][c] *= lam[r >> shift]
+  void* X;
+  int rows, cols, ld;
+  const double* lam;
+  int shift;
+};
+
+struct CholProb {       // X = (chol(G + s I))^{-H}, s = shift_rel * trace(G)
+  const void* G;
+  int ldg, l;
+  double shift_rel;
+  void* X;
+  int ldx;
+  double2* work;        // 2 l^2 complex128
+  int* status;
+  double dead_rel;      // pivots below dead_rel * trace drop their column (0: never)
+  int* dead;            // l flags (scratch)
+};
+
+struct WNormProb {      // out += sum lam[r >> shift]^2 |X[r][c]|^2
+  const void* X;
+  int rows, cols, ld;
+  const double* lam;
+  int shift;
+  double* out;
+};
+
+cudaError_t launch_gauss(void* out, long long count, uint64_t seed, uint64_t stream, cudaStream_t s);
+cudaError_t launch_rowscale(const RowScaleProb* d_probs, int n, long long max_elems, cudaStream_t s);
+cudaError_t launch_chol_inv(const CholProb* d_probs, int n, cudaStream_t s);
+cudaError_t launch_wnorm(const WNormProb* d_probs, int n, long long max_elems, cudaStream_t s);
 
 struct GatherProb {
   const void* src;     // V (ld) or Rfull (ld)

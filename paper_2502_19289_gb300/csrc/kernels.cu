@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
       }
       if (P.kw && k0 + kk < P.K) {
         const double wk = P.kw[(k0 + kk) >> P.kw_shift];
-        v = cscale(v, wk * wk);
+        v = cscale(v, P.kw_pow == 1 ? wk : wk * wk);
       }
       As[kk][m] = v;
       int n;
@@ -561,9 +561,12 @@ __global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ pro
   if (threadIdx.x == 0) {
     double W = 0;
     for (int i = 0; i < n; i++) W += key[i] > 0 ? key[i] : 0.0;
+    P.res[5] = W;         // weight inside the n directions
+    double outside = 0;   // weight outside the n directions (sketched split)
+    if (P.W_ext && *P.W_ext > W) { outside = *P.W_ext - W; W = *P.W_ext; }
     int r = n;
     if (cutoff > 0) {
-      double tail = 0;
+      double tail = outside;
       r = 1;
       for (int i = n - 1; i >= 1; i--) {
         tail += key[i] > 0 ? key[i] : 0.0;

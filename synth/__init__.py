@@ -239,7 +239,7 @@ def spectrum(chi: int, rng: np.random.Generator) -> np.ndarray:
     return np.sqrt(w)
 
 
-def random_right_canonical(n: int, chi: int, seed: int, dtype=np.complex128):
+def random_right_canonical(n: int, chi: int, seed: int, dtype=np.complex128, chis=None):
     """Random MPS: Haar-random right isometries B_q (chi_q, 2, chi_{q+1}) and spectra.
 
     Returns (chi[n+1], sites list, lambdas list).  Rows of every
@@ -248,7 +248,7 @@ def random_right_canonical(n: int, chi: int, seed: int, dtype=np.complex128):
     Schmidt values of a saturated state (used for sizing and timing).
     """
     rng = np.random.default_rng(seed)
-    chis = bond_dims_saturated(n, chi)
+    chis = bond_dims_saturated(n, chi) if chis is None else np.asarray(chis, dtype=np.int64)
     sites, lams = [], []
     for q in range(n):
         cl, cr = int(chis[q]), int(chis[q + 1])
