@@ -214,6 +214,43 @@ int mps_split_log(const ctebd_mps* mps, double* rows, int cap, int* n_rows);
    check failed) since mps_create: out[0], out[1]. */
 int mps_sketch_stats(const ctebd_mps* mps, double* out);
 
+/* ---- Learned rank predictor (sizes the sketched split; not in the paper) ----
+   A network F=16 -> 64 -> 64 -> 16 (ReLU, FP32) maps cheap per-split
+   features to a bucket b of the ratio rank / Eq.-9 bound, ratio in
+   (2^-(b+1)/2, 2^-b/2]; the hint is bound * 2^-b/2.  Parameters are packed
+   W1 (64x16), b1, W2 (64x64), b2, W3 (16x64), b3, row-major. */
+
+/* Features of every split of cluster c (k-1 rows of 16 floats, bond q0+1
+   first), each divided by 10 except j/k: k, j/k, log2 chi_L, log2 chi_R,
+   log2 chi_b, log2 rows, log2 cols, log2 Eq.-9 bound, two-qubit gates
+   crossing the bond, two-qubit gates in the cluster, non-Clifford one-qubit
+   gates, non-Clifford two-qubit gates, layers in the window, entropy of bond
+   b, entropy of the left bond (bits), -log10(cutoff).  entropy: n+1 bond entropies (mps_bond_entropies).
+   Host function.  Errors: ARG. */
+int rank_features(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c, const int* chi,
+                  const double* entropy, const ctebd_config* cfg, float* out);
+
+/* Von Neumann entropy (bits) of every bond spectrum, n+1 doubles. */
+int mps_bond_entropies(ctebd_mps* mps, double* out);
+
+/* Copy n = 6288 parameters (host FP32) to the handle's device model. */
+int rank_model_load(ctebd_mps* mps, const float* weights, size_t n);
+
+/* Forward pass for B feature rows (host); hints_out[i] = ceil(bounds[i] *
+   2^-b/2) for the arg-max bucket b.  Errors: STATE (no model loaded). */
+int rank_model_predict(ctebd_mps* mps, const float* features, int B, const int* bounds, int* hints_out);
+
+/* Training kernels on caller-owned device buffers (FP32), stream may be NULL:
+   logits (B x 16) = net(X (B x 16)); grad (6288) and the scalar loss receive
+   the mean softmax cross-entropy against labels y (B ints) and its gradient
+   (both overwritten); one Adam step (lr, 1-based step t) on params with
+   moment buffers m1, m2 (n = 6288). */
+int mlp_nparams_abi(void);
+int mlp_forward(const float* params, const float* X, int B, float* logits, void* stream);
+int mlp_loss_grad(const float* params, const float* X, const int* y, int B, float* grad, float* loss,
+                  void* stream);
+int mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, float lr, int t, void* stream);
+
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0
    stops timing; launch counts and algorithmic flop/byte counts are always

@@ -75,6 +75,15 @@ def _load():
         "ctebd_profile_read": [P, C.POINTER(D), I, C.POINTER(I)],
         "ctebd_kernel_name": [I, C.c_char_p, S],
         "split2_noalloc": [P, P, I, I, I, D, P, P, P, C.POINTER(I), C.POINTER(D), P],
+        "rank_features": [C.POINTER(Gate), I, C.POINTER(Cluster), C.POINTER(I), C.POINTER(D),
+                          C.POINTER(Config), C.POINTER(C.c_float)],
+        "mps_bond_entropies": [P, C.POINTER(D)],
+        "rank_model_load": [P, C.POINTER(C.c_float), S],
+        "rank_model_predict": [P, C.POINTER(C.c_float), I, C.POINTER(I), C.POINTER(I)],
+        "mlp_nparams_abi": [],
+        "mlp_forward": [P, P, I, P, P],
+        "mlp_loss_grad": [P, P, P, I, P, P, P],
+        "mlp_adam": [P, P, P, P, I, C.c_float, I, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -150,6 +159,36 @@ def cluster_rank_bounds(gates, n_gates, cl: Cluster, chi) -> np.ndarray:
     return out[: cl.k - 1]
 
 
+def rank_features(gates, n_gates, cl: Cluster, chi, entropy, cfg: Config) -> np.ndarray:
+    """16 features per split of the cluster (rows: bonds q0+1 .. q0+k-1)."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    ent = np.ascontiguousarray(entropy, dtype=np.float64)
+    out = np.zeros((max(cl.k - 1, 1), 16), dtype=np.float32)
+    _check(_lib.rank_features(gates, n_gates, C.byref(cl), _ip(chi), _dp(ent), C.byref(cfg),
+                              out.ctypes.data_as(C.POINTER(C.c_float))), "rank_features")
+    return out[: cl.k - 1]
+
+
+def mlp_nparams() -> int:
+    return _lib.mlp_nparams_abi()
+
+
+def mlp_forward(params_ptr, X_ptr, B, logits_ptr, stream=None):
+    _check(_lib.mlp_forward(C.c_void_p(params_ptr), C.c_void_p(X_ptr), B, C.c_void_p(logits_ptr),
+                            C.c_void_p(stream or 0)), "mlp_forward")
+
+
+def mlp_loss_grad(params_ptr, X_ptr, y_ptr, B, grad_ptr, loss_ptr, stream=None):
+    _check(_lib.mlp_loss_grad(C.c_void_p(params_ptr), C.c_void_p(X_ptr), C.c_void_p(y_ptr), B,
+                              C.c_void_p(grad_ptr), C.c_void_p(loss_ptr), C.c_void_p(stream or 0)),
+           "mlp_loss_grad")
+
+
+def mlp_adam(params_ptr, grad_ptr, m1_ptr, m2_ptr, n, lr, t, stream=None):
+    _check(_lib.mlp_adam(C.c_void_p(params_ptr), C.c_void_p(grad_ptr), C.c_void_p(m1_ptr),
+                         C.c_void_p(m2_ptr), n, C.c_float(lr), t, C.c_void_p(stream or 0)), "mlp_adam")
+
+
 def cluster_unitary(gates, n_gates, cl: Cluster) -> np.ndarray:
     D = 1 << cl.k
     U = np.zeros(2 * D * D)
@@ -209,6 +248,24 @@ class MPS:
         sp = (C.c_void_p * len(site_ptrs))(*site_ptrs)
         lp = (C.c_void_p * len(lam_ptrs))(*lam_ptrs)
         _check(_lib.mps_load_device(self._h, _ip(chi), sp, lp), "mps_load_device")
+
+    def bond_entropies(self) -> np.ndarray:
+        out = np.zeros(self.n + 1)
+        _check(_lib.mps_bond_entropies(self._h, _dp(out)), "mps_bond_entropies")
+        return out
+
+    def load_rank_model(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_lib.rank_model_load(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+               "rank_model_load")
+
+    def predict_hints(self, features, bounds) -> np.ndarray:
+        X = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, 16)
+        b = np.ascontiguousarray(bounds, dtype=np.int32)
+        out = np.zeros(len(b), dtype=np.int32)
+        _check(_lib.rank_model_predict(self._h, X.ctypes.data_as(C.POINTER(C.c_float)), len(b),
+                                       _ip(b), _ip(out)), "rank_model_predict")
+        return out
 
     def fidelity(self) -> float:
         F = C.c_double(0)
@@ -314,13 +371,14 @@ def run_iteration(mps: MPS, circ: Circuit, start: int, hint_fn=None):
     """One cluster-TEBD iteration (Sec. III.A) from layer ``start``.
 
     With sketching enabled (FP32, sketch_oversample > 0) each cluster gets
-    rank hints: ``hint_fn(cluster, chi)`` if given (the learned predictor),
-    else the Eq. 9 bound.  Returns (clusters, stop layer, per-split f)."""
+    rank hints: ``hint_fn(clusters, chi)`` if given (the learned predictor,
+    see ``rank_model.make_hint_fn``), else the Eq. 9 bound.  Returns (clusters, stop layer, per-split f)."""
     chi = mps.bond_dims()
     clusters, stop = cluster_partition(circ.gates, circ.n_gates, start, chi, mps.cfg)
-    if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32:
-        for c in clusters:
-            hint = hint_fn(c, chi) if hint_fn else cluster_rank_bounds(circ.gates, circ.n_gates, c, chi)
+    if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32 and clusters:
+        hints = (hint_fn(clusters, chi) if hint_fn else
+                 [cluster_rank_bounds(circ.gates, circ.n_gates, c, chi) for c in clusters])
+        for c, hint in zip(clusters, hints):
             for j, h in enumerate(hint[:11]):
                 c.rank_hint[j] = int(h)
     mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)

@@ -317,11 +317,11 @@ struct Work {
 // ---------------------------------------------------------------------------
 enum KernelKind {
   KK_GEMM_MERGE, KK_GEMM_U, KK_GEMM_GRAM, KK_GEMM_PROJ, KK_EIG_INIT, KK_EIG_INNER, KK_EIG_APPLY,
-  KK_COLNORM, KK_SELECT, KK_GATHER, KK_ONEQ, KK_AMP, KK_GEMM_SKETCH, KK_CHOL, KK_COUNT
+  KK_COLNORM, KK_SELECT, KK_GATHER, KK_ONEQ, KK_AMP, KK_GEMM_SKETCH, KK_CHOL, KK_MLP, KK_COUNT
 };
 static const char* kKindNames[KK_COUNT] = {
   "gemm_merge", "gemm_apply_u", "gemm_gram", "gemm_project", "eig_init", "eig_inner", "eig_apply",
-  "colnorm", "select", "gather", "apply_1q", "amplitude", "gemm_sketch", "cholqr"};
+  "colnorm", "select", "gather", "apply_1q", "amplitude", "gemm_sketch", "cholqr", "mlp_forward"};
 
 struct Prof {
   bool on = false;
@@ -393,6 +393,7 @@ struct ctebd_mps {
   std::vector<double> splitlog2;   // per split: sketched, eigen-dim, rank before cap, hint
   double sk_stats[2] = {0, 0};     // sketched splits attempted, fallen back
   uint64_t nstep = 0;
+  float* mlp = nullptr;            // rank predictor parameters (device)
   void* arena = nullptr;
   size_t arena_cap = 0;
   Staging stage;
@@ -484,6 +485,7 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   for (void* p : m->site) if (p) cudaFree(p);
   for (double* p : m->lam) if (p) cudaFree(p);
   if (m->arena) cudaFree(m->arena);
+  if (m->mlp) cudaFree(m->mlp);
   if (m->h_res) cudaFreeHost(m->h_res);
   m->stage.release();
   m->prof.release();
@@ -1500,5 +1502,139 @@ extern "C" int ctebd_profile_read(ctebd_mps* m, double* rows, int cap, int* n_ki
 extern "C" int ctebd_kernel_name(int kind, char* buf, size_t n) {
   if (kind < 0 || kind >= KK_COUNT || !buf || !n) return fail(CTEBD_ERR_ARG, "ctebd_kernel_name: bad kind");
   std::snprintf(buf, n, "%s", kKindNames[kind]);
+  return CTEBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned rank predictor (sizes the sketched split; not in the paper)
+// ---------------------------------------------------------------------------
+static bool is_nonclifford(int kind) {
+  return kind == CTEBD_T || kind == CTEBD_P || kind == CTEBD_X14 || kind == CTEBD_SQW || kind == CTEBD_CH ||
+         kind == CTEBD_CS || kind == CTEBD_CT || kind == CTEBD_SQSWAP || kind == CTEBD_CP;
+}
+
+extern "C" int rank_features(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c, const int* chi,
+                             const double* entropy, const ctebd_config* cfg, float* out) {
+  if (!c || !chi || !entropy || !cfg || !out || c->k < 2 || c->k > 12 || n_gates < 0 || (n_gates && !gates))
+    return fail(CTEBD_ERR_ARG, "rank_features: bad args");
+  const int k = c->k, q0 = c->q0;
+  std::vector<int> bound(k - 1);
+  TRY(cluster_rank_bounds(gates, n_gates, c, chi, bound.data()));
+  std::vector<int> cross(k, 0);
+  int n2 = 0, nc1 = 0, nc2 = 0;
+  for (int i = 0; i < n_gates; i++) {
+    const ctebd_gate& g = gates[i];
+    if (g.layer <= c->layer_lo || g.layer > c->layer_hi) continue;
+    int lo = g.q[0], hi = g.q[0];
+    for (int t = 1; t < g.n_q; t++) { lo = std::min(lo, g.q[t]); hi = std::max(hi, g.q[t]); }
+    if (lo < q0 || hi >= q0 + k) continue;
+    if (g.n_q >= 2) {
+      n2++;
+      if (is_nonclifford(g.kind)) nc2++;
+      for (int b = lo + 1; b <= hi; b++) cross[b - q0]++;
+    } else if (is_nonclifford(g.kind)) {
+      nc1++;
+    }
+  }
+  auto lg = [](double x) { return (float)std::log2(std::max(x, 1.0)); };
+  for (int j = 1; j < k; j++) {
+    float* f = out + (size_t)(j - 1) * MLP_F;
+    f[0] = (float)k / 10.f;
+    f[1] = (float)j / (float)k;
+    f[2] = lg(chi[q0]) / 10.f;
+    f[3] = lg(chi[q0 + k]) / 10.f;
+    f[4] = lg(chi[q0 + j]) / 10.f;
+    f[5] = lg((double)chi[q0] * (1 << j)) / 10.f;
+    f[6] = lg((double)chi[q0 + k] * (1 << (k - j))) / 10.f;
+    f[7] = lg(bound[j - 1]) / 10.f;
+    f[8] = (float)cross[j] / 10.f;
+    f[9] = (float)n2 / 10.f;
+    f[10] = (float)nc1 / 10.f;
+    f[11] = (float)nc2 / 10.f;
+    f[12] = (float)(c->layer_hi - c->layer_lo) / 10.f;
+    f[13] = (float)entropy[q0 + j] / 10.f;
+    f[14] = (float)entropy[q0] / 10.f;
+    f[15] = cfg->cutoff > 0 ? (float)(-std::log10(cfg->cutoff) / 10.0) : 0.f;
+  }
+  return CTEBD_OK;
+}
+
+extern "C" int mps_bond_entropies(ctebd_mps* m, double* out) {
+  if (!m || !out) return fail(CTEBD_ERR_ARG, "mps_bond_entropies: null argument");
+  const int nb = m->n + 1;
+  double* d = nullptr;
+  CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * nb, m->stream));
+  const double* const* dl; const int* dc;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->stage.reset();
+  std::vector<const double*> lp(m->lam.begin(), m->lam.end());
+  TRY(m->stage.push(lp.data(), lp.size(), (const double* const**)&dl));
+  TRY(m->stage.push(m->chi.data(), nb, &dc));
+  CUDA_TRY(launch_entropy(dl, dc, nb, d, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaFreeAsync(d, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+extern "C" int rank_model_load(ctebd_mps* m, const float* weights, size_t n) {
+  if (!m || !weights) return fail(CTEBD_ERR_ARG, "rank_model_load: null argument");
+  if (n != (size_t)mlp_nparams())
+    return fail(CTEBD_ERR_ARG, "rank_model_load: expected " + std::to_string(mlp_nparams()) + " parameters");
+  if (!m->mlp) CUDA_TRY(cudaMalloc(&m->mlp, sizeof(float) * n));
+  CUDA_TRY(cudaMemcpyAsync(m->mlp, weights, sizeof(float) * n, cudaMemcpyHostToDevice, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return CTEBD_OK;
+}
+
+// hints_out[i] = ceil(bounds[i] * 2^(-b/2)) for the predicted bucket b (the
+// upper edge of the bucket: ratio r / bound in (2^-(b+1)/2, 2^-b/2])
+extern "C" int rank_model_predict(ctebd_mps* m, const float* features, int B, const int* bounds, int* hints_out) {
+  if (!m || B < 0 || (B && (!features || !bounds || !hints_out))) return fail(CTEBD_ERR_ARG, "rank_model_predict: bad args");
+  if (!m->mlp) return fail(CTEBD_ERR_STATE, "rank_model_predict: no model loaded");
+  if (B == 0) return CTEBD_OK;
+  float *dX = nullptr, *dL = nullptr;
+  CUDA_TRY(cudaMallocAsync(&dX, sizeof(float) * B * MLP_F, m->stream));
+  CUDA_TRY(cudaMallocAsync(&dL, sizeof(float) * B * MLP_NB, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(dX, features, sizeof(float) * B * MLP_F, cudaMemcpyHostToDevice, m->stream));
+  {
+    ProfScope ps(m->prof, m->stream, KK_MLP, 2.0 * B * (MLP_F * MLP_H1 + MLP_H1 * MLP_H2 + MLP_H2 * MLP_NB), 0);
+    CUDA_TRY(launch_mlp_forward(m->mlp, dX, B, dL, m->stream));
+  }
+  std::vector<float> lo((size_t)B * MLP_NB);
+  CUDA_TRY(cudaMemcpyAsync(lo.data(), dL, sizeof(float) * lo.size(), cudaMemcpyDeviceToHost, m->stream));
+  CUDA_TRY(cudaFreeAsync(dX, m->stream));
+  CUDA_TRY(cudaFreeAsync(dL, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  for (int i = 0; i < B; i++) {
+    int best = 0;
+    for (int b = 1; b < MLP_NB; b++) if (lo[(size_t)i * MLP_NB + b] > lo[(size_t)i * MLP_NB + best]) best = b;
+    hints_out[i] = std::max(1, (int)std::ceil(bounds[i] * std::pow(2.0, -0.5 * best)));
+  }
+  return CTEBD_OK;
+}
+
+// training entry points on caller-owned device buffers (FP32)
+extern "C" int mlp_nparams_abi(void) { return mlp_nparams(); }
+
+extern "C" int mlp_forward(const float* params, const float* X, int B, float* logits, void* stream) {
+  if (!params || !X || !logits || B < 0) return fail(CTEBD_ERR_ARG, "mlp_forward: bad args");
+  CUDA_TRY(launch_mlp_forward(params, X, B, logits, (cudaStream_t)stream));
+  return CTEBD_OK;
+}
+
+extern "C" int mlp_loss_grad(const float* params, const float* X, const int* y, int B, float* grad, float* loss,
+                             void* stream) {
+  if (!params || !X || !y || !grad || !loss || B < 0) return fail(CTEBD_ERR_ARG, "mlp_loss_grad: bad args");
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * mlp_nparams(), s));
+  CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), s));
+  CUDA_TRY(launch_mlp_loss_grad(params, X, y, B, grad, loss, s));
+  return CTEBD_OK;
+}
+
+extern "C" int mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, float lr, int t, void* stream) {
+  if (!params || !grad || !m1 || !m2 || n != mlp_nparams() || t < 1) return fail(CTEBD_ERR_ARG, "mlp_adam: bad args");
+  CUDA_TRY(launch_adam(params, grad, m1, m2, n, lr, t, (cudaStream_t)stream));
   return CTEBD_OK;
 }

@@ -136,6 +136,15 @@ cudaError_t launch_convert_from_c128(const double* src, void* dst, long long n, 
 template <typename R>
 cudaError_t launch_convert_to_c128(const void* src, double* dst, long long n, cudaStream_t s);
 
+// rank predictor network (features -> hidden -> hidden -> rank buckets)
+constexpr int MLP_F = 16, MLP_H1 = 64, MLP_H2 = 64, MLP_NB = 16;
+int mlp_nparams();
+cudaError_t launch_mlp_forward(const float* params, const float* X, int B, float* logits, cudaStream_t s);
+cudaError_t launch_mlp_loss_grad(const float* params, const float* X, const int* y, int B, float* grad,
+                                 float* loss, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int t, cudaStream_t s);
+cudaError_t launch_entropy(const double* const* d_lams, const int* d_chi, int nb, double* d_out, cudaStream_t s);
+
 // message returned by ctebd_last_error() in the calling thread
 void set_last_error(const std::string& msg);
 

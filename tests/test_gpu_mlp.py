@@ -1,0 +1,120 @@
+"""GPU: the learned rank predictor -- its hand-written kernels against the FP64
+oracle network, training on pairs logged from the full split, and what the
+trained network gains over sizing the sketch with the Eq. 9 bound alone."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import as_oracle, lib
+
+pytestmark = pytest.mark.gpu
+F, H1, H2, NB = 16, 64, 64, 16
+
+
+def _torch():
+    return pytest.importorskip("torch")
+
+
+def test_forward_and_gradient_match_oracle():
+    torch = _torch()
+    P = lib()
+    import paper_2502_19289_gb300.rank_model as R
+    rng = np.random.default_rng(0)
+    params = R.init_params(3) + 0.05 * rng.standard_normal(P.mlp_nparams()).astype(np.float32)
+    B = 300
+    X = rng.standard_normal((B, F)).astype(np.float32)
+    y = rng.integers(0, NB, B).astype(np.int32)
+    dev = torch.device("cuda")
+    Pd, Xd, yd = (torch.as_tensor(a, device=dev) for a in (params, X, y))
+    lo = torch.zeros((B, NB), device=dev)
+    P.mlp_forward(Pd.data_ptr(), Xd.data_ptr(), B, lo.data_ptr())
+    G = torch.zeros(P.mlp_nparams(), device=dev)
+    L = torch.zeros(1, device=dev)
+    P.mlp_loss_grad(Pd.data_ptr(), Xd.data_ptr(), yd.data_ptr(), B, G.data_ptr(), L.data_ptr())
+    torch.cuda.synchronize()
+    p64 = params.astype(np.float64)
+    lo_ref = oracle.mlp_forward(p64, X.astype(np.float64), F, H1, H2, NB)
+    loss_ref, g_ref = oracle.mlp_loss_grad(p64, X.astype(np.float64), y, F, H1, H2, NB)
+    np.testing.assert_allclose(lo.cpu().numpy(), lo_ref, rtol=1e-4, atol=1e-4)
+    assert abs(L.item() - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+    g = G.cpu().numpy()
+    scale = np.abs(g_ref).max()
+    np.testing.assert_allclose(g, g_ref, atol=2e-5 * scale + 1e-7)
+
+
+def _dataset(seeds, sizes=((2, 20, 110, 32), (3, 30, 100, 64))):
+    import paper_2502_19289_gb300.rank_model as R
+    Xs, rs, bs = [], [], []
+    for cfg_id, n, L, chi in sizes:
+        w = synth.reduced(cfg_id, n, L)
+        for s in seeds:
+            c = w.circuit(s, cfg_id)
+            X, r, b = R.collect((c.gates, c.params), n, chi, max(w.cutoff, 1e-10), w.q_max, w.k_max)
+            Xs.append(X); rs.append(r); bs.append(b)
+    return np.concatenate(Xs), np.concatenate(rs), np.concatenate(bs)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    _torch()
+    import paper_2502_19289_gb300.rank_model as R
+    Xtr, rtr, btr = _dataset(range(1, 9))
+    Xte, rte, bte = _dataset(range(41, 44))
+    ytr, yte = R.bucket_of(rtr, btr), R.bucket_of(rte, bte)
+    params, hist = R.train(Xtr, ytr, epochs=150, lr=3e-3, batch=256, seed=0)
+    return dict(params=params, hist=hist, Xte=Xte, yte=yte, rte=rte, bte=bte, ytr=ytr)
+
+
+def test_training_reduces_loss_and_predicts_held_out(trained):
+    import paper_2502_19289_gb300.rank_model as R
+    P = lib()
+    hist = trained["hist"]
+    assert hist[-1] < 0.5 * hist[0]
+    m = P.MPS(P.make_config(4, 4, 0.0, 10, 0, 0, P.FP32))
+    m.load_rank_model(trained["params"])
+    hints = m.predict_hints(trained["Xte"], trained["bte"])
+    pred = R.bucket_of(np.maximum(hints, 1), trained["bte"])
+    acc = float(np.mean(np.abs(pred - trained["yte"]) <= 1))
+    # majority-class baseline from the training labels
+    maj = np.bincount(trained["ytr"], minlength=NB).argmax()
+    base = float(np.mean(np.abs(maj - trained["yte"]) <= 1))
+    assert acc >= base and acc >= 0.5, (acc, base)
+
+
+def _run(P, c, w, chi, over, hint_fn_factory=None):
+    circ = P.Circuit(c.n_qubits, c.gates, c.params)
+    cfg = P.make_config(c.n_qubits, chi, max(w.cutoff, 1e-10), w.q_max, 0, w.k_max, P.FP32,
+                        sketch_oversample=over)
+    mps = P.MPS(cfg)
+    hf = hint_fn_factory(mps, circ, cfg) if hint_fn_factory else None
+    start, work, n_sk = 0, 0.0, 0
+    while start < circ.n_layers:
+        clusters, stop, f = P.run_iteration(mps, circ, start, hf)
+        if clusters:
+            log = mps.split_log()
+            work += float(np.sum(log[:, 9] ** 3))        # eigen-solve work ~ dimension^3
+            n_sk += int(log[:, 8].sum())
+        start = stop
+    return mps, work, n_sk
+
+
+def test_learned_hints_gain_over_eq9_bound(trained):
+    """Held-out circuit: both sizings reproduce the oracle; the learned sizes
+    sketch more splits and shrink the eigen-solve work."""
+    import paper_2502_19289_gb300.rank_model as R
+    P = lib()
+    w = synth.reduced(2, 20, 110)
+    c = w.circuit(45, 2)
+    chi = 32
+    ref = oracle.simulate(c, chi, w.cutoff, w.q_max, 0, w.k_max)
+    m0, work0, sk0 = _run(P, c, w, chi, 0)
+    mb, workb, skb = _run(P, c, w, chi, 4)
+    ml, workl, skl = _run(P, c, w, chi, 4,
+                          lambda mps, circ, cfg: R.make_hint_fn(mps, circ, cfg, trained["params"]))
+    for mm in (m0, mb, ml):
+        assert abs(ref.overlap(as_oracle(mm))) >= 1 - 1e-6
+        assert abs(mm.fidelity() / np.exp(ref.logF) - 1) <= 1e-5
+    assert workl <= workb <= work0
+    assert skl >= skb
+    assert workl < work0
