@@ -170,6 +170,21 @@ def plain_fp64_update(torch, sites, lams, q0, k, U, chi_max, cutoff):
     return fs
 
 
+def aggregate(dev_s: float, wall_s: float, units: int, device=None):
+    """Whole-job figures over all ranks: max of the times, sum of the units.
+
+    Replicas share nothing on the data path; this is the only collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dev_s, wall_s, units
+    t = torch.tensor([dev_s, wall_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(round(float(u[0])))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -353,13 +368,7 @@ def main():
     units = res["updates"]
     wall = res["wall_s"]
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s, wall], device=f"cuda:{local_rank}", dtype=torch.float64)
-        u = torch.tensor([units], device=f"cuda:{local_rank}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        dev_s, wall = float(t[0]), float(t[1])
-        units = int(u[0])
+        dev_s, wall, units = aggregate(dev_s, wall, units, device=f"cuda:{local_rank}")
     if rank != 0:
         if world > 1:
             import torch.distributed as dist

@@ -397,3 +397,74 @@ def simulate(circ: Circuit, cfg: Config, stream=None, callback=None, hint_fn=Non
             callback(start, stop, clusters, f)
         start = stop
     return mps
+
+
+class PackedCircuits:
+    """Independent circuits laid side by side on one MPS (cfg5-style packing).
+
+    Circuit i occupies qubits [offset_i, offset_i + n_i); no gate crosses the
+    boundaries, so the bonds between circuits stay at dimension 1.  Every
+    circuit keeps its own partition and stop layer (Sec. III.A applied per
+    circuit); one iteration advances every unfinished circuit by one of its
+    own iterations, and the clusters of all circuits go into the same batched
+    launches."""
+
+    def __init__(self, circuits):
+        self.locals = []
+        self.offsets = []
+        off = 0
+        rows, params = [], []
+        for n, gates5, prm in circuits:
+            g = np.asarray(gates5, dtype=np.int32).reshape(-1, 5).copy()
+            self.locals.append(Circuit(n, g, prm))
+            self.offsets.append(off)
+            gs = g.copy()
+            for col in (1, 2, 3):
+                gs[:, col] = np.where(gs[:, col] >= 0, gs[:, col] + off, -1)
+            rows.append(gs)
+            params.append(np.asarray(prm, dtype=np.float64))
+            off += n
+        self.n = off
+        self.globals = [Circuit(self.n, r, p) for r, p in zip(rows, params)]
+        self.start = [0] * len(circuits)
+
+    def done(self) -> bool:
+        return all(s >= c.n_layers for s, c in zip(self.start, self.locals))
+
+    def iteration(self, mps: "MPS", cfg_local):
+        """One iteration of every unfinished circuit; returns clusters stepped."""
+        chi = mps.bond_dims()
+        all_clusters, Us = [], []
+        for i, (loc, glob, off) in enumerate(zip(self.locals, self.globals, self.offsets)):
+            if self.start[i] >= loc.n_layers:
+                continue
+            cfg_local.n_qubits = loc.n
+            cl, stop = cluster_partition(loc.gates, loc.n_gates, self.start[i], chi[off:off + loc.n + 1],
+                                         cfg_local)
+            for c in cl:
+                c.q0 += off
+            mps.apply_singletons(glob.gates, glob.n_gates, cl, self.start[i], stop)
+            if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32:
+                for c in cl:
+                    for j, h in enumerate(cluster_rank_bounds(glob.gates, glob.n_gates, c, chi)[:11]):
+                        c.rank_hint[j] = int(h)
+            Us.extend(cluster_unitary(glob.gates, glob.n_gates, c) for c in cl)
+            all_clusters.extend(cl)
+            self.start[i] = stop
+        if all_clusters:
+            mps.step(all_clusters, Us)
+        return all_clusters
+
+
+def simulate_packed(circuits, cfg: Config, stream=None, callback=None):
+    """Run several independent circuits packed on one MPS; returns (mps, packing)."""
+    pk = PackedCircuits(circuits)
+    big = Config.from_buffer_copy(cfg)
+    big.n_qubits = pk.n
+    mps = MPS(big, stream)
+    local = Config.from_buffer_copy(cfg)
+    while not pk.done():
+        cl = pk.iteration(mps, local)
+        if callback:
+            callback(cl)
+    return mps, pk

@@ -1096,22 +1096,35 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
       }
       full_sel.push_back(a);
     }
-    if (!sk_sel.empty()) {
-      TRY(level_sketch(m, ws, L, sk_sel, step_key));
+    // sketched splits: tail check on the weight outside the sketch (must be
+    // below max(cutoff, 1e-6) W); a rejected sketch is retried once with twice
+    // the columns when that still fits in half the width, then falls back to
+    // the full eigen-solve
+    for (int round = 0; round < 2 && !sk_sel.empty(); round++) {
+      TRY(level_sketch(m, ws, L, sk_sel, step_key * 2 + round));
       TRY(level_solve(m, ws, L, sk_sel));
-      // tail check: weight outside the sketch must be below max(cutoff, 1e-6) W;
-      // otherwise the split falls back to the full eigen-solve
       const double tol = std::max(m->cfg.cutoff, 1e-6);
+      std::vector<int> retry;
       for (int a : sk_sel) {
         const double* res = m->h_res + 16 * a;
         const double Wt = res[2], inside = res[5];
         m->sk_stats[0] += 1;
-        if (!(Wt - inside <= tol * Wt)) {
-          m->sk_stats[1] += 1;
-          level_set_full(L, a, JB);
-          full_sel.push_back(a);
+        if (Wt - inside <= tol * Wt) continue;
+        Work& w = ws[L.act[a]];
+        const int l2 = 2 * L.ne[a];
+        if (round == 0 && 2 * l2 <= L.nn[a] && (size_t)L.mm[a] * l2 <= w.bufElems / 2) {
+          L.ne[a] = l2;
+          L.nepad[a] = (int)round_up(l2, 2 * JB);
+          L.nbv[a] = L.nepad[a] / JB;
+          L.vld[a] = L.nepad[a];
+          retry.push_back(a);
+          continue;
         }
+        m->sk_stats[1] += 1;
+        level_set_full(L, a, JB);
+        full_sel.push_back(a);
       }
+      sk_sel.swap(retry);
     }
     TRY(level_solve(m, ws, L, full_sel));
     // write back: new right sites, unweighted remainders
