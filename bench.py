@@ -122,7 +122,7 @@ def saturated_state(P, mps, n, chi, seed, device):
 
 def profile_rows(P, mps):
     import ctypes as C
-    rows = np.zeros(4 * 32)
+    rows = np.zeros(5 * 32)
     nk = C.c_int(0)
     P._check(P.lib.ctebd_profile_read(mps._h, rows.ctypes.data_as(C.POINTER(C.c_double)), 32,
                                       C.byref(nk)), "profile_read")
@@ -130,7 +130,8 @@ def profile_rows(P, mps):
     for k in range(nk.value):
         buf = C.create_string_buffer(64)
         P.lib.ctebd_kernel_name(k, buf, 64)
-        out[buf.value.decode()] = dict(zip(("launches", "ms", "flops", "bytes"), rows[4 * k:4 * k + 4]))
+        out[buf.value.decode()] = dict(zip(("launches", "ms", "flops", "bytes", "tc_launches"),
+                                           rows[5 * k:5 * k + 5]))
     return out
 
 

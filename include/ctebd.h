@@ -251,12 +251,24 @@ int mlp_loss_grad(const float* params, const float* X, const int* y, int B, floa
                   void* stream);
 int mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, float lr, int t, void* stream);
 
+/* C (M x N) = A (M x K) B (K x N) on the tensor cores (tcgen05, 3xTF32 for
+   FP32 accuracy); complex64 row-major device buffers, M % 128 == 0,
+   N % 64 == 0, K % 16 == 0.  Building block of the tensor-core paths, exposed
+   for validation.  Errors: ARG, CUDA, TIMEOUT (bounded completion wait). */
+int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* stream);
+
+/* Tensor-core policy for the FP32 complex GEMMs (merge, U, Gram, projections,
+   sketches), process-wide: 0 never, 1 (default) calls above 2 GFLOP of
+   work, 2 always.  FP64 GEMMs always use the CUDA cores. */
+int ctebd_set_tensor_cores(int mode);
+
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0
    stops timing; launch counts and algorithmic flop/byte counts are always
-   kept).  ctebd_profile_read writes, per kernel class k < cap, the row
-   (launches, total ms, algorithmic flops, algorithmic bytes) at rows[4k]
-   and the number of classes in *n_kinds; ctebd_kernel_name names class k.
+   kept).  ctebd_profile_read writes one row per kernel class k < cap and the
+   number of classes in *n_kinds; ctebd_kernel_name names class k.
+   Rows are (launches, total ms, algorithmic flops, algorithmic bytes,
+   launches that ran on the tensor cores) at rows[5k].
    Not part of the paper: instrumentation of this implementation. */
 int ctebd_profile(ctebd_mps* mps, int mode);
 int ctebd_profile_read(ctebd_mps* mps, double* rows, int cap, int* n_kinds);

@@ -81,6 +81,8 @@ def _load():
         "rank_model_load": [P, C.POINTER(C.c_float), S],
         "rank_model_predict": [P, C.POINTER(C.c_float), I, C.POINTER(I), C.POINTER(I)],
         "mlp_nparams_abi": [],
+        "tc_cgemm": [P, P, P, I, I, I, P],
+        "ctebd_set_tensor_cores": [I],
         "mlp_forward": [P, P, I, P, P],
         "mlp_loss_grad": [P, P, P, I, P, P, P],
         "mlp_adam": [P, P, P, P, I, C.c_float, I, P],
@@ -167,6 +169,17 @@ def rank_features(gates, n_gates, cl: Cluster, chi, entropy, cfg: Config) -> np.
     _check(_lib.rank_features(gates, n_gates, C.byref(cl), _ip(chi), _dp(ent), C.byref(cfg),
                               out.ctypes.data_as(C.POINTER(C.c_float))), "rank_features")
     return out[: cl.k - 1]
+
+
+def set_tensor_cores(mode: int):
+    """FP32 GEMM policy: 0 CUDA cores only, 1 above 2 GFLOP (default), 2 always."""
+    _check(_lib.ctebd_set_tensor_cores(int(mode)), "ctebd_set_tensor_cores")
+
+
+def tc_cgemm(A_ptr, B_ptr, C_ptr, M, K, N, stream=None):
+    """Complex64 product on the tensor cores (validation of the tile engine)."""
+    _check(_lib.tc_cgemm(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr), M, K, N,
+                         C.c_void_p(stream or 0)), "tc_cgemm")
 
 
 def mlp_nparams() -> int:

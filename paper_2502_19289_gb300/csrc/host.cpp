@@ -329,6 +329,7 @@ struct Prof {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   double launches[KK_COUNT] = {0}, ms[KK_COUNT] = {0}, flops[KK_COUNT] = {0}, bytes[KK_COUNT] = {0};
+  double tc[KK_COUNT] = {0};   // launches of the class that ran on the tensor cores
   cudaEvent_t get() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -336,7 +337,7 @@ struct Prof {
     return e;
   }
   void reset() {
-    for (int i = 0; i < KK_COUNT; i++) launches[i] = ms[i] = flops[i] = bytes[i] = 0;
+    for (int i = 0; i < KK_COUNT; i++) launches[i] = ms[i] = flops[i] = bytes[i] = tc[i] = 0;
   }
   // fold finished records into the accumulators (caller synchronised)
   void drain() {
@@ -394,6 +395,7 @@ struct ctebd_mps {
   double sk_stats[2] = {0, 0};     // sketched splits attempted, fallen back
   uint64_t nstep = 0;
   float* mlp = nullptr;            // rank predictor parameters (device)
+  int* tc_err = nullptr;           // tensor-core completion-wait timeout flag (device)
   void* arena = nullptr;
   size_t arena_cap = 0;
   Staging stage;
@@ -486,6 +488,7 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   for (double* p : m->lam) if (p) cudaFree(p);
   if (m->arena) cudaFree(m->arena);
   if (m->mlp) cudaFree(m->mlp);
+  if (m->tc_err) cudaFree(m->tc_err);
   if (m->h_res) cudaFreeHost(m->h_res);
   m->stage.release();
   m->prof.release();
@@ -497,21 +500,42 @@ extern "C" int mps_destroy(ctebd_mps* m) {
 // ---------------------------------------------------------------------------
 // Batched pieces
 // ---------------------------------------------------------------------------
+// tensor-core GEMM policy: 0 never, 1 for FP32 calls above a work threshold,
+// 2 for every FP32 call (process-wide; ctebd_set_tensor_cores)
+static int g_tc_mode = 1;
+
+extern "C" int ctebd_set_tensor_cores(int mode) {
+  if (mode < 0 || mode > 2) return fail(CTEBD_ERR_ARG, "ctebd_set_tensor_cores: mode 0, 1 or 2");
+  g_tc_mode = mode;
+  return CTEBD_OK;
+}
+
 static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind) {
   if (probs.empty()) return CTEBD_OK;
-  std::vector<long long> off(probs.size() + 1, 0);
   double fl = 0, by = 0;
-  for (size_t i = 0; i < probs.size(); i++) {
-    const GemmProb& g = probs[i];
-    off[i + 1] = off[i] + gemm_tiles(g, m->fp64);
+  for (const GemmProb& g : probs) {
     fl += 8.0 * g.M * g.N * (double)g.K * g.batch;
     by += ((double)g.M * g.K * (g.sA ? g.batch : 1) + (double)g.K * g.N * (g.sB ? g.batch : 1) +
            (double)g.M * g.N * g.batch) * m->esz;
   }
+  const bool tc = !m->fp64 && (g_tc_mode == 2 || (g_tc_mode == 1 && fl >= 2e9));
+  std::vector<long long> off(probs.size() + 1, 0);
+  for (size_t i = 0; i < probs.size(); i++)
+    off[i + 1] = off[i] + (tc ? tc_gemm_tiles(probs[i]) : gemm_tiles(probs[i], m->fp64));
   const GemmProb* dp;
   const long long* doff;
   TRY(m->stage.push(probs.data(), probs.size(), &dp));
   TRY(m->stage.push(off.data(), off.size(), &doff));
+  if (tc) {
+    if (!m->tc_err) {
+      CUDA_TRY(cudaMalloc(&m->tc_err, sizeof(int)));
+      CUDA_TRY(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
+    }
+    ProfScope ps(m->prof, m->stream, kind, fl, by);
+    m->prof.tc[kind] += 1;
+    CUDA_TRY(launch_tc_gemm(dp, doff, (int)probs.size(), off.back(), m->tc_err, m->stream));
+    return CTEBD_OK;
+  }
   ProfScope ps(m->prof, m->stream, kind, fl, by);
   cudaError_t e = m->fp64 ? launch_gemm<double>(dp, doff, (int)probs.size(), off.back(), m->stream)
                           : launch_gemm<float>(dp, doff, (int)probs.size(), off.back(), m->stream);
@@ -1186,6 +1210,16 @@ static int make_work(ctebd_mps* m, const ctebd_cluster* c, Work& w) {
   return CTEBD_OK;
 }
 
+// a tensor-core completion wait that ran out sets the flag; report and clear it
+static int check_tc_flag(ctebd_mps* m) {
+  if (!m->tc_err) return CTEBD_OK;
+  int h = 0;
+  CUDA_TRY(cudaMemcpy(&h, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return CTEBD_OK;
+  CUDA_TRY(cudaMemset(m->tc_err, 0, sizeof(int)));
+  return fail(CTEBD_ERR_TIMEOUT, "a tensor-core completion wait timed out");
+}
+
 extern "C" int step(ctebd_mps* m, const ctebd_cluster* c, int n, const double* const* U, double* f_out) {
   if (!m || n < 0 || (n > 0 && (!c || !U))) return fail(CTEBD_ERR_ARG, "step: bad args");
   if (n == 0) return CTEBD_OK;
@@ -1208,6 +1242,7 @@ extern "C" int step(ctebd_mps* m, const ctebd_cluster* c, int n, const double* c
   std::vector<std::vector<double>> fs;
   TRY(split_levels(m, ws, fs, ++m->nstep));
   CUDA_TRY(cudaStreamSynchronize(m->stream));
+  TRY(check_tc_flag(m));
   if (f_out) {
     size_t o = 0;
     for (int i = 0; i < n; i++) for (double f : fs[i]) f_out[o++] = f;
@@ -1504,10 +1539,11 @@ extern "C" int ctebd_profile_read(ctebd_mps* m, double* rows, int cap, int* n_ki
   m->prof.drain();
   *n_kinds = KK_COUNT;
   for (int k = 0; k < KK_COUNT && k < cap && rows; k++) {
-    rows[4 * k + 0] = m->prof.launches[k];
-    rows[4 * k + 1] = m->prof.ms[k];
-    rows[4 * k + 2] = m->prof.flops[k];
-    rows[4 * k + 3] = m->prof.bytes[k];
+    rows[5 * k + 0] = m->prof.launches[k];
+    rows[5 * k + 1] = m->prof.ms[k];
+    rows[5 * k + 2] = m->prof.flops[k];
+    rows[5 * k + 3] = m->prof.bytes[k];
+    rows[5 * k + 4] = m->prof.tc[k];
   }
   return CTEBD_OK;
 }
@@ -1649,5 +1685,24 @@ extern "C" int mlp_loss_grad(const float* params, const float* X, const int* y, 
 extern "C" int mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, float lr, int t, void* stream) {
   if (!params || !grad || !m1 || !m2 || n != mlp_nparams() || t < 1) return fail(CTEBD_ERR_ARG, "mlp_adam: bad args");
   CUDA_TRY(launch_adam(params, grad, m1, m2, n, lr, t, (cudaStream_t)stream));
+  return CTEBD_OK;
+}
+
+// C (M x N) = A (M x K) B (K x N), complex64 row-major device buffers, on the
+// tensor cores (3xTF32); M % 128 == 0, N % 64 == 0, K % 32 == 0.  Used to
+// validate the tile engine against a reference product.
+extern "C" int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* stream) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 64 || K % 16)
+    return fail(CTEBD_ERR_ARG, "tc_cgemm: M % 128, N % 64, K % 16 must be 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = nullptr;
+  CUDA_TRY(cudaMallocAsync(&err, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  CUDA_TRY(launch_tc_plain(A, B, C, M, K, N, err, s));
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaFreeAsync(err, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h) return fail(CTEBD_ERR_TIMEOUT, "tc_cgemm: tensor-core completion wait timed out");
   return CTEBD_OK;
 }

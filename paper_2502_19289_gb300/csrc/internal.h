@@ -145,6 +145,13 @@ cudaError_t launch_mlp_loss_grad(const float* params, const float* X, const int*
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int t, cudaStream_t s);
 cudaError_t launch_entropy(const double* const* d_lams, const int* d_chi, int nb, double* d_out, cudaStream_t s);
 
+// tensor-core (tcgen05, 3xTF32) complex tile products
+cudaError_t launch_tc_plain(const void* A, const void* B, void* C, int M, int K, int N, int* err,
+                            cudaStream_t s);
+long long tc_gemm_tiles(const GemmProb& p);
+cudaError_t launch_tc_gemm(const GemmProb* d_probs, const long long* d_tile_off, int n_probs,
+                           long long total_tiles, int* err, cudaStream_t s);
+
 // message returned by ctebd_last_error() in the calling thread
 void set_last_error(const std::string& msg);
 
