@@ -206,7 +206,8 @@ int mps_load_device(ctebd_mps* mps, const int* chi, const void* const* sites,
 
 /* Per-split log of the last step() / truncate_split: rows of 12 doubles
    (q0, k, bond, m, n, r, f, W, sketched, eigen-dimension, rank before the
-   chi_max cap, rank hint).  *n_rows receives the row count; up to cap rows
+   chi_max cap, rank hint, Jacobi sweeps of the first pass, Jacobi sweeps of
+   the FP32 refinement pass) -- 14 doubles per row.  *n_rows receives the row count; up to cap rows
    are written. */
 int mps_split_log(const ctebd_mps* mps, double* rows, int cap, int* n_rows);
 

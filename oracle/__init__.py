@@ -163,6 +163,34 @@ def svd_right(M: np.ndarray):
     return s, Y.view(np.complex128).reshape(n, p)
 
 
+def truncation_rank(s: np.ndarray, chi_max: int, cutoff: float, floor: float) -> int:
+    """Rank kept by one truncated split (Sec. II.C, Eqs. 4-5): the smallest r
+    whose discarded weight sum_{i>=r} s_i^2 stays within cutoff * sum s_i^2,
+    then no more than the values above floor * s_0, at most chi_max, at least 1."""
+    s2 = np.asarray(s, dtype=np.float64) ** 2
+    W = s2.sum()
+    r = len(s2)
+    if cutoff > 0:
+        tail = np.cumsum(s2[::-1])[::-1]          # tail[i] = sum_{j>=i} s_j^2
+        over = np.nonzero(tail[1:] > cutoff * W)[0]
+        r = int(over[-1]) + 2 if len(over) else 1
+    r = min(r, int(np.sum(s > floor * s[0])), chi_max)
+    return max(r, 1)
+
+
+def split_fidelity(M: np.ndarray, w: np.ndarray, chi_max: int, cutoff: float, floor: float = 1e-13):
+    """One truncated split of the Schmidt-weighted matrix diag(w) M (Sec. II.C):
+    returns (r, f, W, s) with s the singular values of diag(w) M, W = sum s^2,
+    r the kept rank and f = sum_{i<r} s_i^2 / W the split's fidelity (Eq. 4).
+    The SVD is LAPACK's (numpy), a library step; sizes up to a few thousand."""
+    A = np.asarray(w, dtype=np.float64)[:, None] * np.asarray(M, dtype=np.complex128)
+    s = np.linalg.svd(A, compute_uv=False)
+    r = truncation_rank(s, chi_max, cutoff, floor)
+    W = float(np.sum(s * s))
+    f = float(np.sum(s[:r] ** 2) / W) if W > 0 else 1.0
+    return r, f, W, s
+
+
 # ---- MPS (Vidal form, Sec. II.B-II.C, III.A) --------------------------------
 class MPS:
     """Oracle MPS: right-canonical sites B_q (chi_q, 2, chi_{q+1}) + spectra."""

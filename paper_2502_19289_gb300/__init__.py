@@ -295,9 +295,9 @@ class MPS:
     def split_log(self) -> np.ndarray:
         n = C.c_int(0)
         _check(_lib.mps_split_log(self._h, None, 0, C.byref(n)), "mps_split_log")
-        rows = np.zeros(12 * max(n.value, 1))
+        rows = np.zeros(14 * max(n.value, 1))
         _check(_lib.mps_split_log(self._h, _dp(rows), n.value, C.byref(n)), "mps_split_log")
-        return rows[: 12 * n.value].reshape(-1, 12)
+        return rows[: 14 * n.value].reshape(-1, 14)
 
     def sketch_stats(self):
         out = np.zeros(2)

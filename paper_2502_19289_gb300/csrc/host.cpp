@@ -293,7 +293,7 @@ struct Work {
   void* W = nullptr;     // refinement accumulator
   void* J = nullptr;
   size_t eigElems = 0, jElems = 0;
-  double* rho = nullptr;
+  double* rho = nullptr;   // nmax weights, then nmax squared column norms of V
   int* perm = nullptr;
   double* res = nullptr; // [0..7] select results, [8] ||M||^2, [12..15] int status
   // sketched split (FP32, sketch enabled): Y and Q (m x l), B^H and Q_B (n x l),
@@ -391,7 +391,8 @@ struct ctebd_mps {
   int lam_cap = 0;
   double logF = 0;
   std::vector<double> splitlog;
-  std::vector<double> splitlog2;   // per split: sketched, eigen-dim, rank before cap, hint
+  std::vector<double> splitlog2;   // per split: sketched, eigen-dim, rank before cap, hint,
+                                   // Jacobi sweeps of pass 1 and pass 2
   double sk_stats[2] = {0, 0};     // sketched splits attempted, fallen back
   uint64_t nstep = 0;
   float* mlp = nullptr;            // rank predictor parameters (device)
@@ -569,7 +570,7 @@ static std::vector<std::pair<void**, size_t>> work_buffers(const ctebd_mps* m, W
   std::vector<std::pair<void**, size_t>> b = {
       {&w.bufA, w.bufElems * m->esz}, {&w.bufB, w.bufElems * m->esz}, {&w.G, w.eigElems * m->esz},
       {&w.V, w.eigElems * m->esz},    {&w.W, w.eigElems * m->esz},    {&w.J, w.jElems * m->esz},
-      {(void**)&w.rho, w.nmax * 8},   {(void**)&w.perm, w.nmax * 4},  {(void**)&w.res, 256}};
+      {(void**)&w.rho, w.nmax * 16},   {(void**)&w.perm, w.nmax * 4},  {(void**)&w.res, 256}};
   if (!m->fp64 && m->cfg.sketch_oversample > 0) {
     b.push_back({&w.Ys, w.bufElems / 2 * m->esz});
     b.push_back({&w.Qs, w.bufElems / 2 * m->esz});
@@ -691,6 +692,7 @@ struct Level {
   std::vector<int> mm, nn, npad, shift;        // M-bar rows / cols, padded cols, lambda shift
   std::vector<int> ne, nepad, nbv, vld;        // eigen-dimension, padded, blocks, ld of V
   std::vector<char> sk;                        // sketched
+  std::vector<int> sw1, sw2;                   // Jacobi sweeps of pass 1 / pass 2
 };
 
 static void level_set_full(Level& L, int a, int JB) {
@@ -727,25 +729,34 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // rotation floor eps * trace(G): 1 for a Gram computed from Mbar (absolute
 // rounding), ~0 for a Gram of already rotated columns (relative accuracy).
 static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
-                     const std::vector<void*>& acc, double floor_factor) {
+                     const std::vector<void*>& acc, double floor_factor, double rel_skip,
+                     std::vector<int>& sweeps) {
   const bool f64 = m->fp64;
   const int JB = eig_block(f64);
   const int na = (int)sel.size();
   if (na == 0) return CTEBD_OK;
   std::vector<EigProb> eps(na);
-  double* d_off = nullptr;
-  CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * 3 * na, m->stream));
   int max_npad = 0, max_nb = 0;
+  for (int i = 0; i < na; i++) {
+    max_npad = std::max(max_npad, L.nepad[sel[i]]);
+    max_nb = std::max(max_nb, L.nbv[sel[i]]);
+  }
+  const int maxh = std::max(1, max_nb / 2);
+  // per problem: 3 counters (zeroed every sweep), the trace, then maxh pair flags
+  double* d_off = nullptr;
+  const size_t n_dbl = 4 * (size_t)na + ((size_t)na * maxh + 1) / 2;
+  CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * n_dbl, m->stream));
+  int* d_flag = reinterpret_cast<int*>(d_off + 4 * na);
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
     Work& w = ws[L.act[a]];
     eps[i].G = w.G; eps[i].V = acc[i]; eps[i].J = w.J;
     eps[i].npad = L.nepad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
-    eps[i].off = d_off + 2 * i;
-    eps[i].scale = d_off + 2 * na + i;
+    eps[i].off = d_off + 3 * i;
+    eps[i].scale = d_off + 3 * na + i;
     eps[i].floor_factor = floor_factor;
-    max_npad = std::max(max_npad, L.nepad[a]);
-    max_nb = std::max(max_nb, L.nbv[a]);
+    eps[i].jflag = d_flag + (size_t)i * maxh;
+    eps[i].rel_skip = rel_skip;
   }
   const EigProb* dep;
   TRY(m->stage.push(eps.data(), eps.size(), &dep));
@@ -755,20 +766,21 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
                  : launch_eig_init<float>(dep, na, max_npad, m->stream));
     CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
   }
-  std::vector<double> hoff(2 * na);
+  std::vector<double> hoff(3 * na);
   const int max_sweeps = 30;
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
-    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 2 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
+    double fap_sweep = 0, bap_sweep = 0;
     for (int t = 0; t < max_nb - 1; t++) {
-      double bin = 0, fap = 0, bap = 0;
+      double bin = 0;
       const double D = 2.0 * JB;
       for (int i = 0; i < na; i++) {
         const int a = sel[i];
         if (!eps[i].active || t >= L.nbv[a] - 1) continue;
         const double h = L.nbv[a] / 2, np2 = (double)L.nepad[a] * L.nepad[a];
-        bin += 2 * h * D * D * m->esz;                           // read blocks, write J
-        fap += 8.0 * (2 * h * (h + 1) / 2 + h * h) * D * D * D;  // J^H G J (upper tiles), V J
-        bap += (4 * np2 + h * D * D) * m->esz;                   // G, V read+write, J read
+        bin += 2 * h * D * D * m->esz;                                 // read blocks, write J
+        fap_sweep += 8.0 * (2 * h * (h + 1) / 2 + h * h) * D * D * D;  // J^H G J (upper tiles), V J
+        bap_sweep += (4 * np2 + h * D * D) * m->esz;                   // G, V read+write, J read
       }
       {
         ProfScope ps(m->prof, m->stream, KK_EIG_INNER, 0, bin);
@@ -776,20 +788,26 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
                      : launch_eig_inner<float>(dep, na, max_nb, t, m->stream));
       }
       {
-        ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, fap, bap);
+        // flops and bytes are added after the sweep from the tiles actually updated
+        ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, 0, 0);
         CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
                      : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
       }
     }
-    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, m->stream));
     CUDA_TRY(cudaStreamSynchronize(m->stream));
     bool any = false;
+    double fap_done = 0;
     for (int i = 0; i < na; i++) {
+      if (eps[i].active) sweeps[sel[i]] += 1;
       // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
-      m->prof.flops[KK_EIG_INNER] += hoff[2 * i + 1] * 42.0 * (2 * JB);
+      m->prof.flops[KK_EIG_INNER] += hoff[3 * i + 1] * 42.0 * (2 * JB);
+      fap_done += hoff[3 * i + 2];
       if (!eps[i].active) continue;
-      if (hoff[2 * i] == 0.0) eps[i].active = 0; else any = true;
+      if (hoff[3 * i] == 0.0) eps[i].active = 0; else any = true;
     }
+    m->prof.flops[KK_EIG_APPLY] += fap_done;
+    if (fap_sweep > 0) m->prof.bytes[KK_EIG_APPLY] += bap_sweep * (fap_done / fap_sweep);
     if (!any) break;
     m->stage.reset();
     TRY(m->stage.push(eps.data(), eps.size(), &dep));
@@ -817,33 +835,40 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
     p.C = w.bufB; p.ldc = L.ne[a]; p.alpha = 1.0;
     probs.push_back(p);
     CUDA_TRY(cudaMemsetAsync(w.rho, 0, sizeof(double) * L.ne[a], m->stream));
+    CUDA_TRY(cudaMemsetAsync(w.rho + w.nmax, 0, sizeof(double) * L.ne[a], m->stream));
     max_n = std::max(max_n, L.ne[a]);
-    max_m = std::max(max_m, L.mm[a]);
+    max_m = std::max(max_m, std::max(L.mm[a], L.nn[a]));
   }
   TRY(run_gemms(m, probs, KK_GEMM_PROJ));
   {
-    std::vector<const void*> R(na);
-    std::vector<const double*> Lm(na);
-    std::vector<double*> rho(na);
-    std::vector<int> mm(na), nn(na), sh(na);
+    // problems 0..na-1: weighted column norms of Rfull (rho); na..2na-1:
+    // squared column norms of V (vn), which normalise rho and the write-back
+    std::vector<const void*> R(2 * na);
+    std::vector<const double*> Lm(2 * na);
+    std::vector<double*> rho(2 * na);
+    std::vector<int> mm(2 * na), nn(2 * na), sh(2 * na), ld(2 * na);
     double by = 0;
     for (int i = 0; i < na; i++) {
       const int a = sel[i];
       Work& w = ws[L.act[a]];
       R[i] = w.bufB; Lm[i] = m->lam[w.q0]; rho[i] = w.rho;
-      mm[i] = L.mm[a]; nn[i] = L.ne[a]; sh[i] = L.shift[a];
-      by += (double)mm[i] * nn[i] * m->esz;
+      mm[i] = L.mm[a]; nn[i] = L.ne[a]; sh[i] = L.shift[a]; ld[i] = L.ne[a];
+      R[na + i] = w.V; Lm[na + i] = nullptr; rho[na + i] = w.rho + w.nmax;
+      mm[na + i] = L.nn[a]; nn[na + i] = L.ne[a]; sh[na + i] = 0; ld[na + i] = L.vld[a];
+      by += ((double)L.mm[a] + L.nn[a]) * L.ne[a] * m->esz;
     }
-    const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
-    TRY(m->stage.push(R.data(), na, (const void* const**)&dR));
-    TRY(m->stage.push(mm.data(), na, &dm));
-    TRY(m->stage.push(nn.data(), na, &dn));
-    TRY(m->stage.push(sh.data(), na, &dsh));
-    TRY(m->stage.push(Lm.data(), na, (const double* const**)&dL));
-    TRY(m->stage.push(rho.data(), na, (double* const**)&drho));
+    const void* const* dR; const int *dm, *dn, *dsh, *dld; const double* const* dL; double* const* drho;
+    TRY(m->stage.push(R.data(), 2 * na, (const void* const**)&dR));
+    TRY(m->stage.push(mm.data(), 2 * na, &dm));
+    TRY(m->stage.push(nn.data(), 2 * na, &dn));
+    TRY(m->stage.push(sh.data(), 2 * na, &dsh));
+    TRY(m->stage.push(ld.data(), 2 * na, &dld));
+    TRY(m->stage.push(Lm.data(), 2 * na, (const double* const**)&dL));
+    TRY(m->stage.push(rho.data(), 2 * na, (double* const**)&drho));
     ProfScope ps(m->prof, m->stream, KK_COLNORM, 0, by);
-    CUDA_TRY(f64 ? launch_colnorm_batch<double>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream)
-                 : launch_colnorm_batch<float>(dR, dm, dn, dL, dsh, drho, na, max_n, max_m, m->stream));
+    CUDA_TRY(f64 ? launch_colnorm_batch<double>(dR, dm, dn, dld, dL, dsh, drho, 2 * na, max_n, max_m, m->stream)
+                 : launch_colnorm_batch<float>(dR, dm, dn, dld, dL, dsh, drho, 2 * na, max_n, max_m, m->stream));
+    CUDA_TRY(launch_rho_normalize(drho, drho + na, dn, na, max_n, m->stream));
   }
   std::vector<SelProb> sp(na);
   for (int i = 0; i < na; i++) {
@@ -1027,7 +1052,7 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
     accV.push_back(L.sk[a] ? w.W : w.V);
   }
   TRY(level_gram(m, ws, L, sel, Z));
-  TRY(level_eig(m, ws, L, sel, accV, 1.0));
+  TRY(level_eig(m, ws, L, sel, accV, 1.0, 4.0, L.sw1));
   // sketched problems: V = Q_B W (n x l, ld nepad) into V
   {
     std::vector<GemmProb> probs;
@@ -1045,15 +1070,19 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
   }
   TRY(level_project_select(m, ws, L, sel));
   if (f64) return CTEBD_OK;
-  // pass 2 (FP32): where the cutoff or the zero floor -- not chi_max -- decided
-  // the rank, the weights of the small directions must be accurate relative to
-  // their own size: re-diagonalise the freshly computed Gram of the rotated
-  // columns Z = M V and rotate V and Z by the result.
+  // pass 2 (FP32).  Pass 1 resolves the spectrum of G only to an absolute
+  // level of about eps * trace(G): a kept direction p of weight rho_p can keep
+  // couplings of that size to discarded ones and so lose up to
+  // ~ n (eps trace)^2 / rho_p of its weight -- summed over the kept set this
+  // exceeds 1e-5 of the total for n ~ 2048 with a flat spectrum, whether the
+  // cutoff or chi_max decides the rank.  Re-diagonalise the freshly computed
+  // Gram of the rotated columns Z = M V (whose rounding is relative to each
+  // column's own weight) with relative thresholds only, and rotate V and Z by
+  // the result.  Rotations below 32 eps sqrt(a d) are skipped: the weight they
+  // could move is below n (32 eps)^2 of the total.
   std::vector<int> ref;
-  for (int a : sel) {
-    const int r = (int)m->h_res[16 * a];
-    if (r < std::min(m->cfg.chi_max, L.ne[a])) ref.push_back(a);
-  }
+  for (int a : sel)   // nothing to refine where every direction is kept
+    if ((int)m->h_res[16 * a] < L.ne[a]) ref.push_back(a);
   if (ref.empty()) return CTEBD_OK;
   std::vector<const void*> Z2;
   std::vector<void*> accW;
@@ -1062,7 +1091,7 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
     accW.push_back(ws[L.act[a]].W);
   }
   TRY(level_gram(m, ws, L, ref, Z2));
-  TRY(level_eig(m, ws, L, ref, accW, 1e-12));
+  TRY(level_eig(m, ws, L, ref, accW, 1e-12, 32.0, L.sw2));
   std::vector<GemmProb> probs;
   for (int a : ref) {
     Work& w = ws[L.act[a]];
@@ -1094,6 +1123,8 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
     const int na = (int)L.act.size();
     for (auto* v : {&L.mm, &L.nn, &L.npad, &L.shift, &L.ne, &L.nepad, &L.nbv, &L.vld}) v->resize(na);
     L.sk.assign(na, 0);
+    L.sw1.assign(na, 0);
+    L.sw2.assign(na, 0);
     std::vector<int> sk_sel, full_sel;
     for (int a = 0; a < na; a++) {
       Work& w = ws[L.act[a]];
@@ -1167,10 +1198,12 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
       TRY(ensure_site(m, bnd, (size_t)r * L.nn[a]));
       GatherProb g0{};
       g0.src = w.V; g0.dst = m->site[bnd]; g0.perm = w.perm; g0.rows = L.nn[a]; g0.r = r; g0.ld = L.vld[a]; g0.mode = 0;
+      g0.cs = w.rho + w.nmax;
       gp.push_back(g0);
       GatherProb g1{};
       g1.src = w.bufB; g1.dst = w.bufA; g1.perm = w.perm; g1.rows = L.mm[a]; g1.r = r; g1.ld = L.ne[a]; g1.mode = 1;
       g1.scale = 1.0 / std::sqrt(kept);
+      g1.cs = w.rho + w.nmax;
       gp.push_back(g1);
       maxe = std::max(maxe, std::max((long long)r * L.nn[a], (long long)r * L.mm[a]));
       m->chi[bnd] = r;
@@ -1179,8 +1212,9 @@ static int split_levels(ctebd_mps* m, std::vector<Work>& ws, std::vector<std::ve
       fs[L.act[a]].push_back(f);
       const double row[8] = {(double)w.q0, (double)w.k, (double)bnd, (double)L.mm[a], (double)L.nn[a], (double)r, f, W};
       m->splitlog.insert(m->splitlog.end(), row, row + 8);
-      const double extra[4] = {(double)L.sk[a], (double)L.ne[a], res[4], (double)w.hint[j - 1]};
-      m->splitlog2.insert(m->splitlog2.end(), extra, extra + 4);
+      const double extra[6] = {(double)L.sk[a], (double)L.ne[a], res[4], (double)w.hint[j - 1],
+                               (double)L.sw1[a], (double)L.sw2[a]};
+      m->splitlog2.insert(m->splitlog2.end(), extra, extra + 6);
     }
     const GatherProb* dgp;
     TRY(m->stage.push(gp.data(), gp.size(), &dgp));
@@ -1479,8 +1513,8 @@ extern "C" int mps_split_log(const ctebd_mps* m, double* rows, int cap, int* n_r
   *n_rows = nr;
   if (rows)
     for (int i = 0; i < std::min(nr, cap); i++) {
-      std::memcpy(rows + 12 * i, m->splitlog.data() + 8 * i, sizeof(double) * 8);
-      std::memcpy(rows + 12 * i + 8, m->splitlog2.data() + 4 * i, sizeof(double) * 4);
+      std::memcpy(rows + 14 * i, m->splitlog.data() + 8 * i, sizeof(double) * 8);
+      std::memcpy(rows + 14 * i + 8, m->splitlog2.data() + 6 * i, sizeof(double) * 6);
     }
   return CTEBD_OK;
 }

@@ -38,9 +38,12 @@ struct EigProb {
   int npad;
   int nb;       // number of JB-blocks, even
   int active;   // 0: converged, skip
-  double* off;         // [0] significant rotations this sweep, [1] all rotations
+  double* off;         // [0] significant rotations this sweep, [1] all rotations,
+                       // [2] flops of the tile updates actually applied (when jflag set)
   const double* scale; // trace of G (noise floor of the rotations)
   double floor_factor; // absolute rotation floor = eps * trace * floor_factor
+  int* jflag;          // per pair slot: 1 when its J_p is not the identity; null: always apply
+  double rel_skip;     // relative rotation floor in units of eps (0: 4)
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -94,6 +97,7 @@ struct GatherProb {
   int mode;            // 0: site = conj(V[c][perm[mu]]) -> dst[mu][c] (rows = n)
                        // 1: rem  = Rfull[row][perm[mu]] * scale -> dst[row][mu]
   double scale;
+  const double* cs;    // per source column scale (1 / |v_j|), or null
 };
 
 // Launchers (R = float or double).  Descriptor arrays are device pointers.
@@ -116,10 +120,12 @@ template <typename R>
 cudaError_t launch_eig_trace(const EigProb* d_probs, int n_probs, cudaStream_t s);
 
 template <typename R>
-cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n,
+cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n, const int* d_ld,
                                  const double* const* d_lam, const int* d_shift,
                                  double* const* d_rho, int n_probs, int max_n, int max_m,
                                  cudaStream_t s);
+cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, const int* d_n, int n_probs,
+                                 int max_n, cudaStream_t s);
 cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff,
                           double floor2, cudaStream_t s);
 template <typename R>

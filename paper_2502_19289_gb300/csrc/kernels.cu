@@ -171,13 +171,13 @@ __device__ __forceinline__ void circle(int t, int i, int N, int& a, int& b) {
 // sweep loop going) when the relative coupling |g| / sqrt(a d) exceeds
 // sqrt(eps) and |g| is well above the absolute noise floor.
 template <typename R>
-__device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R floor_abs, R& c, R& s,
-                                            typename C2<R>::T& ph, bool& skip, bool& signif) {
+__device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R floor_abs, R rel_skip, R& c,
+                                            R& s, typename C2<R>::T& ph, bool& skip, bool& signif) {
   using CT = typename C2<R>::T;
   const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
   const R ag = sqrt(g.x * g.x + g.y * g.y);
   const R rad = sqrt(fabs(a * d));
-  skip = !(ag > (R)4 * eps * rad) || !(ag > floor_abs) || ag == (R)0;
+  skip = !(ag > rel_skip * eps * rad) || !(ag > floor_abs) || ag == (R)0;
   signif = !skip && ag > sqrt(eps) * rad && ag > (R)8 * floor_abs;
   if (skip) { c = 1; s = 0; ph = cmk<CT>(1, 0); return; }
   const R zeta = (d - a) / ((R)2 * ag);
@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
   extern __shared__ unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
   CT* Q = A + D * LD;
-  R* cs = reinterpret_cast<R*>(Q + D * LD);
-  R* sn = cs + JB;
+  R* tu = reinterpret_cast<R*>(Q + D * LD);   // tan(theta / 2) of each rotation
+  R* sn = tu + JB;
   CT* ph = reinterpret_cast<CT*>(sn + JB);
   int* pp = reinterpret_cast<int*>(ph + JB);
   int* pq = pp + JB;
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
   }
   const R eps_r = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
   const R floor_abs = (R)((double)eps_r * (*P.scale) * P.floor_factor);
+  const R rel_skip = P.rel_skip > 0 ? (R)P.rel_skip : (R)4;
   __syncthreads();
   int total = 0, total_sig = 0;
   const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
@@ -229,33 +230,38 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
         circle(r, threadIdx.x, D, p, q);
         pp[threadIdx.x] = p; pq[threadIdx.x] = q;
         R c, s; CT e; bool skip, sig;
-        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, c, s, e, skip, sig);
-        cs[threadIdx.x] = c; sn[threadIdx.x] = s; ph[threadIdx.x] = e;
+        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip,
+                       sig);
+        tu[threadIdx.x] = s / ((R)1 + c); sn[threadIdx.x] = s; ph[threadIdx.x] = e;
         if (!skip) atomicAdd(&nrot, 1);
         if (sig) atomicAdd(&nsig, 1);
       }
       __syncthreads();
+      // x' = c x - s y, y' = s x + c y in Rutishauser's form
+      //   x' = x - s (y + tau x),  y' = y + s (x - tau y),  tau = s / (1 + c):
+      // for small angles c = 1 - s tau is not rounded to 1, which would grow
+      // every vector by (1 + t^2) per rotation in FP32
       for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of A and Q
         const int row = e / JB, k = e % JB;
         const int p = pp[k], q = pq[k];
-        const R c = cs[k], s = sn[k];
+        const R t = tu[k], s = sn[k];
         const CT f = ph[k];
         CT x = A[row * LD + p], y = cmul(A[row * LD + q], f);
-        A[row * LD + p] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
-        A[row * LD + q] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+        A[row * LD + p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
+        A[row * LD + q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
         x = Q[row * LD + p]; y = cmul(Q[row * LD + q], f);
-        Q[row * LD + p] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
-        Q[row * LD + q] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+        Q[row * LD + p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
+        Q[row * LD + q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
       }
       __syncthreads();
       for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // rows of A
         const int col = e / JB, k = e % JB;
         const int p = pp[k], q = pq[k];
-        const R c = cs[k], s = sn[k];
+        const R t = tu[k], s = sn[k];
         const CT f = cconj(ph[k]);
         CT x = A[p * LD + col], y = cmul(A[q * LD + col], f);
-        A[p * LD + col] = cmk<CT>(c * x.x - s * y.x, c * x.y - s * y.y);
-        A[q * LD + col] = cmk<CT>(s * x.x + c * y.x, s * x.y + c * y.y);
+        A[p * LD + col] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
+        A[q * LD + col] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
       }
       __syncthreads();
     }
@@ -265,8 +271,13 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
     __syncthreads();
     if (nr == 0) break;
   }
-  CT* Jo = (CT*)P.J + (long long)blockIdx.x * D * D;
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) Jo[e] = Q[(e / D) * LD + (e % D)];
+  // no rotation at all leaves Q exactly the identity: flag it so that the
+  // apply step skips the multiply (and J need not be written)
+  if (P.jflag && threadIdx.x == 0) P.jflag[blockIdx.x] = total > 0;
+  if (!P.jflag || total > 0) {
+    CT* Jo = (CT*)P.J + (long long)blockIdx.x * D * D;
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) Jo[e] = Q[(e / D) * LD + (e % D)];
+  }
   if (threadIdx.x == 0 && total > 0) {
     atomicAdd(P.off, (double)total_sig);
     atomicAdd(P.off + 1, (double)total);
@@ -296,6 +307,11 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
     Pp = (tile - nG) / h;
     Qp = (tile - nG) % h;
   }
+  // tiles whose rotations are all the identity are left as they are
+  const bool fq = !P.jflag || P.jflag[Qp], fp = isG && (!P.jflag || P.jflag[Pp]);
+  if (!fq && !fp) return;
+  if (P.jflag && threadIdx.x == 0)
+    atomicAdd(P.off + 2, 8.0 * D * D * D * ((fq ? 1 : 0) + (fp ? 1 : 0)));
   int K1, K2, I1 = 0, I2 = 0;
   circle(round, Qp, P.nb, K1, K2);
   if (isG) circle(round, Pp, P.nb, I1, I2);
@@ -311,7 +327,7 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
   for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
     const int li = e / D, lj = e % D;
     S0[li * LD + lj] = X[grow(li) * P.npad + gcol(lj)];
-    S1[li * LD + lj] = Jb[(long long)Qp * D * D + e];
+    if (fq) S1[li * LD + lj] = Jb[(long long)Qp * D * D + e];
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -319,8 +335,8 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
 #pragma unroll
   for (int i = 0; i < PER; i++)
 #pragma unroll
-    for (int j = 0; j < PER; j++) acc[i][j] = cmk<CT>(0, 0);
-  for (int k = 0; k < D; k++) {          // T = X_tile * J_Q
+    for (int j = 0; j < PER; j++) acc[i][j] = fq ? cmk<CT>(0, 0) : S0[(ty + 16 * i) * LD + tx + 16 * j];
+  if (fq) for (int k = 0; k < D; k++) {  // T = X_tile * J_Q
     CT a[PER], b[PER];
 #pragma unroll
     for (int i = 0; i < PER; i++) a[i] = S0[(ty + 16 * i) * LD + k];
@@ -344,14 +360,15 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
   for (int i = 0; i < PER; i++)
 #pragma unroll
     for (int j = 0; j < PER; j++) S0[(ty + 16 * i) * LD + tx + 16 * j] = acc[i][j];
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x)
-    S1[(e / D) * LD + (e % D)] = Jb[(long long)Pp * D * D + e];
+  if (fp)
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x)
+      S1[(e / D) * LD + (e % D)] = Jb[(long long)Pp * D * D + e];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < PER; i++)
 #pragma unroll
-    for (int j = 0; j < PER; j++) acc[i][j] = cmk<CT>(0, 0);
-  for (int k = 0; k < D; k++) {          // Y = J_P^H * T
+    for (int j = 0; j < PER; j++) acc[i][j] = fp ? cmk<CT>(0, 0) : S0[(ty + 16 * i) * LD + tx + 16 * j];
+  if (fp) for (int k = 0; k < D; k++) {  // Y = J_P^H * T
     CT a[PER], b[PER];
 #pragma unroll
     for (int i = 0; i < PER; i++) a[i] = cconj(S1[k * LD + ty + 16 * i]);
@@ -479,11 +496,13 @@ constexpr int CN_ROWS = 256;
 
 template <typename R>
 __global__ void k_colnorm(const void* const* __restrict__ Rs, const int* __restrict__ ms,
-                          const int* __restrict__ ns, const double* const* __restrict__ lams,
-                          const int* __restrict__ shifts, double* const* __restrict__ rhos) {
+                          const int* __restrict__ ns, const int* __restrict__ lds,
+                          const double* const* __restrict__ lams, const int* __restrict__ shifts,
+                          double* const* __restrict__ rhos) {
   using CT = typename C2<R>::T;
   const int p = blockIdx.z;
   const int n = ns[p], m = ms[p];
+  const long long ld = lds ? lds[p] : n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r0 = blockIdx.y * CN_ROWS;
   if (c >= n || r0 >= m) return;
@@ -493,29 +512,53 @@ __global__ void k_colnorm(const void* const* __restrict__ Rs, const int* __restr
   const int r1 = min(m, r0 + CN_ROWS);
   double acc = 0;
   for (int r = r0; r < r1; r++) {
-    const CT v = Rm[(long long)r * n + c];
-    const double w = lam[r >> sh];
+    const CT v = Rm[(long long)r * ld + c];
+    const double w = lam ? lam[r >> sh] : 1.0;
     acc += w * w * ((double)v.x * v.x + (double)v.y * v.y);
   }
   atomicAdd(&rhos[p][c], acc);
 }
 
 template <typename R>
-cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n,
+cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const int* d_n, const int* d_ld,
                                  const double* const* d_lam, const int* d_shift,
                                  double* const* d_rho, int n_probs, int max_n, int max_m,
                                  cudaStream_t s) {
   if (n_probs <= 0) return cudaSuccess;
   dim3 grid((max_n + 127) / 128, (max_m + CN_ROWS - 1) / CN_ROWS, n_probs);
-  k_colnorm<R><<<grid, 128, 0, s>>>(d_R, d_m, d_n, d_lam, d_shift, d_rho);
+  k_colnorm<R><<<grid, 128, 0, s>>>(d_R, d_m, d_n, d_ld, d_lam, d_shift, d_rho);
   return cudaGetLastError();
 }
-template cudaError_t launch_colnorm_batch<float>(const void* const*, const int*, const int*,
+template cudaError_t launch_colnorm_batch<float>(const void* const*, const int*, const int*, const int*,
                                                  const double* const*, const int*,
                                                  double* const*, int, int, int, cudaStream_t);
-template cudaError_t launch_colnorm_batch<double>(const void* const*, const int*, const int*,
+template cudaError_t launch_colnorm_batch<double>(const void* const*, const int*, const int*, const int*,
                                                   const double* const*, const int*,
                                                   double* const*, int, int, int, cudaStream_t);
+
+// The accumulated rotations V are orthonormal only to rounding: the weight of
+// direction i is rho_i / |v_i|^2, and the site row / remainder column it
+// yields is scaled by 1 / |v_i|.  rho_i <- rho_i / vn_i, vn_i <- 1 / sqrt(vn_i).
+__global__ void k_rho_normalize(double* const* __restrict__ rhos, double* const* __restrict__ vns,
+                                const int* __restrict__ ns) {
+  const int p = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns[p]) return;
+  const double v = vns[p][i];
+  if (v > 0) {
+    rhos[p][i] /= v;
+    vns[p][i] = 1.0 / sqrt(v);
+  } else {
+    vns[p][i] = 1.0;
+  }
+}
+
+cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, const int* d_n, int n_probs,
+                                 int max_n, cudaStream_t s) {
+  if (n_probs <= 0 || max_n <= 0) return cudaSuccess;
+  k_rho_normalize<<<dim3((max_n + 255) / 256, n_probs), 256, 0, s>>>(d_rho, d_vn, d_n);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Truncation (Sec. II.B): sort the weights descending, keep the smallest r
@@ -625,11 +668,14 @@ __global__ void k_gather(const GatherProb* __restrict__ probs) {
        e += (long long)gridDim.x * blockDim.x) {
     if (P.mode == 0) {
       const int mu = (int)(e / P.rows), c = (int)(e % P.rows);
-      dst[e] = cconj(src[(long long)c * P.ld + P.perm[mu]]);
+      const int j = P.perm[mu];
+      const CT v = cconj(src[(long long)c * P.ld + j]);
+      dst[e] = P.cs ? cscale(v, P.cs[j]) : v;
     } else {
       const long long row = e / P.r;
       const int mu = (int)(e % P.r);
-      dst[e] = cscale(src[row * P.ld + P.perm[mu]], P.scale);
+      const int j = P.perm[mu];
+      dst[e] = cscale(src[row * P.ld + j], P.cs ? P.scale * P.cs[j] : P.scale);
     }
   }
 }

@@ -40,7 +40,7 @@ constexpr size_t NA_OFF_V = NA_OFF_G + al256((size_t)NA_N * NA_N * NA_CPLX);
 constexpr size_t NA_OFF_W = NA_OFF_V + al256((size_t)NA_N * NA_N * NA_CPLX);
 constexpr size_t NA_OFF_J = NA_OFF_W + al256((size_t)NA_N * NA_N * NA_CPLX);
 constexpr size_t NA_OFF_RHO = NA_OFF_J + al256((size_t)NA_N * 2 * NA_JB * NA_CPLX);
-constexpr size_t NA_OFF_PERM = NA_OFF_RHO + al256(NA_N * sizeof(double));
+constexpr size_t NA_OFF_PERM = NA_OFF_RHO + al256(2 * NA_N * sizeof(double));   // rho, then |v_i|^2
 constexpr size_t NA_OFF_RES = NA_OFF_PERM + al256(NA_N * sizeof(int));
 constexpr size_t NA_OFF_CNT = NA_OFF_RES + al256(8 * sizeof(double));
 constexpr size_t NA_OFF_DESC = NA_OFF_CNT + al256(4 * sizeof(double));
@@ -112,12 +112,14 @@ static int na_gemm(NaDesc& d, const GemmProb& p) {
 
 // Block-Jacobi on G (npad x npad) accumulating into acc; same kernels and
 // stopping rule as the handle path.
-static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor) {
+static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor,
+                  double rel_skip) {
   double* cnt = (double*)(S + NA_OFF_CNT);   // [0] significant, [1] all, [2] trace
   EigProb e{};
   e.G = S + NA_OFF_G; e.V = acc; e.J = S + NA_OFF_J;
   e.npad = npad; e.nb = npad / NA_JB; e.active = 1;
   e.off = cnt; e.scale = cnt + 2; e.floor_factor = floor_factor;
+  e.rel_skip = rel_skip;   // no pair flags: every tile is updated
   const EigProb* de;
   const size_t mark = d.off;
   if (int rc = d.put(&e, 1, &de)) return rc;
@@ -147,18 +149,24 @@ static int na_project(NaDesc& d, unsigned char* S, const void* V, int m, int n, 
   p.B = V; p.ldb = npad; p.opB = 0;
   p.C = S + NA_OFF_RFULL; p.ldc = n; p.alpha = 1.0;
   if (int rc = na_gemm(d, p)) return rc;
+  // rho (weighted column norms of Rfull) and |v_i|^2 (column norms of V),
+  // then rho_i / |v_i|^2 as the handle path does
   double* rho = (double*)(S + NA_OFF_RHO);
-  NA_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * n, d.s));
-  const void* R = S + NA_OFF_RFULL;
-  const int shift = 1;
-  const void* const* dR; const int *dm, *dn, *dsh; const double* const* dL; double* const* drho;
-  if (int rc = d.put(&R, 1, (const void* const**)&dR)) return rc;
-  if (int rc = d.put(&m, 1, &dm)) return rc;
-  if (int rc = d.put(&n, 1, &dn)) return rc;
-  if (int rc = d.put(&shift, 1, &dsh)) return rc;
-  if (int rc = d.put(&lamL, 1, (const double* const**)&dL)) return rc;
-  if (int rc = d.put(&rho, 1, (double* const**)&drho)) return rc;
-  NA_CUDA(launch_colnorm_batch<float>(dR, dm, dn, dL, dsh, drho, 1, n, m, d.s));
+  NA_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * 2 * NA_N, d.s));
+  const void* R[2] = {S + NA_OFF_RFULL, V};
+  const int ms[2] = {m, n}, ns[2] = {n, n}, shs[2] = {1, 0}, lds[2] = {n, npad};
+  const double* lams[2] = {lamL, nullptr};
+  double* rhos[2] = {rho, rho + NA_N};
+  const void* const* dR; const int *dm, *dn, *dsh, *dld; const double* const* dL; double* const* drho;
+  if (int rc = d.put(R, 2, (const void* const**)&dR)) return rc;
+  if (int rc = d.put(ms, 2, &dm)) return rc;
+  if (int rc = d.put(ns, 2, &dn)) return rc;
+  if (int rc = d.put(shs, 2, &dsh)) return rc;
+  if (int rc = d.put(lds, 2, &dld)) return rc;
+  if (int rc = d.put(lams, 2, (const double* const**)&dL)) return rc;
+  if (int rc = d.put(rhos, 2, (double* const**)&drho)) return rc;
+  NA_CUDA(launch_colnorm_batch<float>(dR, dm, dn, dld, dL, dsh, drho, 2, n, std::max(m, n), d.s));
+  NA_CUDA(launch_rho_normalize(drho, drho + 1, dn, 1, n, d.s));
   return CTEBD_OK;
 }
 
@@ -196,7 +204,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     if (int rc = na_gemm(d, p)) return rc;
   }
   void* V = S + NA_OFF_V;
-  if (int rc = na_eig(d, S, V, npad, 1.0)) return rc;
+  if (int rc = na_eig(d, S, V, npad, 1.0, 4.0)) return rc;
   double res[8];
   auto select = [&](const void* Vc) -> int {
     if (int rc = na_project(d, S, Vc, m, n, npad, lam_l)) return rc;
@@ -212,8 +220,8 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     return CTEBD_OK;
   };
   if (int rc = select(V)) return rc;
-  // pass 2 when the cutoff or the zero floor (not chi_max) decided the rank
-  if ((int)res[0] < std::min(chi_max, n)) {
+  // pass 2 wherever something is discarded (relative thresholds, as the handle path)
+  if ((int)res[0] < n) {
     NA_CUDA(cudaMemsetAsync(S + NA_OFF_G, 0, (size_t)npad * npad * NA_CPLX, s));
     GemmProb p{};
     p.M = n; p.N = n; p.K = m; p.batch = 1;
@@ -222,7 +230,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     p.C = S + NA_OFF_G; p.ldc = npad;
     p.kw = lam_l; p.kw_shift = 1; p.alpha = 1.0;
     if (int rc = na_gemm(d, p)) return rc;
-    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12)) return rc;
+    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0)) return rc;
     GemmProb q{};
     q.M = n; q.N = n; q.K = n; q.batch = 1;
     q.A = V; q.lda = npad; q.opA = 0;
@@ -239,8 +247,10 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
   GatherProb g[2] = {};
   g[0].src = V; g[0].dst = site_r_out; g[0].perm = (int*)(S + NA_OFF_PERM);
   g[0].rows = n; g[0].r = r; g[0].ld = npad; g[0].mode = 0;
+  g[0].cs = (const double*)(S + NA_OFF_RHO) + NA_N;
   g[1].src = S + NA_OFF_RFULL; g[1].dst = site_l_out; g[1].perm = (int*)(S + NA_OFF_PERM);
   g[1].rows = m; g[1].r = r; g[1].ld = n; g[1].mode = 1; g[1].scale = 1.0 / std::sqrt(kept);
+  g[1].cs = g[0].cs;
   const GatherProb* dg;
   if (int rc = d.put(g, 2, &dg)) return rc;
   NA_CUDA(launch_gather<float>(dg, 2, (long long)std::max(m, n) * r, s));

@@ -32,6 +32,12 @@ def as_oracle(mps) -> oracle.MPS:
     return oracle.MPS.from_arrays(sites, lams)
 
 
+def fidelity_overlap(a: oracle.MPS, b: oracle.MPS) -> float:
+    """|<a|b>| / (|a| |b|): after a truncation the right-canonical form is only
+    approximately normalised (on both sides alike), so states are compared as rays."""
+    return abs(a.overlap(b)) / np.sqrt(abs(a.overlap(a)) * abs(b.overlap(b)))
+
+
 def statevector_of(sites):
     v = np.ones((1, 1), dtype=np.complex128)
     for s in sites:

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import as_oracle, lib
+from gpu_helpers import as_oracle, fidelity_overlap, lib
 
 pytestmark = pytest.mark.gpu
 F, H1, H2, NB = 16, 64, 64, 16
@@ -113,7 +113,7 @@ def test_learned_hints_gain_over_eq9_bound(trained):
     ml, workl, skl = _run(P, c, w, chi, 4,
                           lambda mps, circ, cfg: R.make_hint_fn(mps, circ, cfg, trained["params"]))
     for mm in (m0, mb, ml):
-        assert abs(ref.overlap(as_oracle(mm))) >= 1 - 1e-6
+        assert fidelity_overlap(ref, as_oracle(mm)) >= 1 - 1e-6
         assert abs(mm.fidelity() / np.exp(ref.logF) - 1) <= 1e-5
     assert workl <= workb <= work0
     assert skl >= skb

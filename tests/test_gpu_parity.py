@@ -12,8 +12,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import (as_oracle, contracted, download, entangling_circuit, lib,
-                         random_unitary, run_gpu, statevector_of)
+from gpu_helpers import (as_oracle, contracted, download, entangling_circuit, fidelity_overlap,
+                         lib, random_unitary, run_gpu, statevector_of)
 
 pytestmark = pytest.mark.gpu
 W1 = synth.WORKLOADS[1]
@@ -67,7 +67,7 @@ def test_truncated_run_matches_oracle(precision, ftol, otol):
     assert len(f_gpu) == len(f_ref)
     np.testing.assert_allclose(f_gpu, f_ref, rtol=ftol)
     assert abs(mps.fidelity() - np.exp(ref.logF)) <= ftol * 10
-    ov = abs(ref.overlap(as_oracle(mps)))
+    ov = fidelity_overlap(ref, as_oracle(mps))
     assert ov >= 1 - otol
 
 
@@ -82,7 +82,7 @@ def test_cfg2_shape_reduced_fp32(chi_max):
     mps, log = run_gpu(c, *args, P.FP32)
     ref = oracle.simulate(c, *args)
     assert list(mps.bond_dims()) == list(ref.chi())
-    ov = abs(ref.overlap(as_oracle(mps)))
+    ov = fidelity_overlap(ref, as_oracle(mps))
     assert ov >= 1 - 1e-6
     f_gpu = np.concatenate([f for (_, _, _, f) in log])
     np.testing.assert_allclose(f_gpu, ref.split_log()[:, 7], rtol=1e-5)

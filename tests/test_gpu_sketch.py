@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import as_oracle, contracted, lib, random_unitary, run_gpu
+from gpu_helpers import as_oracle, contracted, fidelity_overlap, lib, random_unitary, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -79,5 +79,5 @@ def test_simulation_with_sketching_matches_oracle():
     ref = oracle.simulate(c, 32, w.cutoff, w.q_max, 0, w.k_max)
     assert n_sk > 0
     assert list(mps.bond_dims()) == list(ref.chi())
-    assert abs(ref.overlap(as_oracle(mps))) >= 1 - 1e-6
+    assert fidelity_overlap(ref, as_oracle(mps)) >= 1 - 1e-6
     assert abs(mps.fidelity() / np.exp(ref.logF) - 1) <= 1e-5

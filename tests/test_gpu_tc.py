@@ -39,7 +39,7 @@ def test_cluster_updates_with_tensor_core_gemms_match_oracle(tensor_cores_forced
     projections): same parity targets as the CUDA-core path."""
     import oracle
     import synth
-    from gpu_helpers import as_oracle, run_gpu
+    from gpu_helpers import as_oracle, fidelity_overlap, run_gpu
     P = lib()
     w = synth.reduced(2, 20, 110)
     c = w.circuit(0, 2)
@@ -48,6 +48,6 @@ def test_cluster_updates_with_tensor_core_gemms_match_oracle(tensor_cores_forced
         mps, log = run_gpu(c, *args, P.FP32)
         ref = oracle.simulate(c, *args)
         assert list(mps.bond_dims()) == list(ref.chi())
-        assert abs(ref.overlap(as_oracle(mps))) >= 1 - 1e-6
+        assert fidelity_overlap(ref, as_oracle(mps)) >= 1 - 1e-6
         f_gpu = np.concatenate([f for (_, _, _, f) in log])
         np.testing.assert_allclose(f_gpu, ref.split_log()[:, 7], rtol=1e-5)
