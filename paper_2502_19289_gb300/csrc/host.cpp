@@ -730,7 +730,7 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // rounding), ~0 for a Gram of already rotated columns (relative accuracy).
 static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
                      const std::vector<void*>& acc, double floor_factor, double rel_skip,
-                     std::vector<int>& sweeps) {
+                     std::vector<int>& sweeps, bool use_cut = false) {
   const bool f64 = m->fp64;
   const int JB = eig_block(f64);
   const int na = (int)sel.size();
@@ -757,6 +757,10 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     eps[i].floor_factor = floor_factor;
     eps[i].jflag = d_flag + (size_t)i * maxh;
     eps[i].rel_skip = rel_skip;
+    if (use_cut) {   // columns sorted by the previous pass: [lo, hi) around the cut
+      eps[i].cut_lo = (int)m->h_res[16 * a + 6];
+      eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
+    }
   }
   const EigProb* dep;
   TRY(m->stage.push(eps.data(), eps.size(), &dep));
@@ -883,7 +887,13 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
   TRY(m->stage.push(sp.data(), na, &dsp));
   {
     ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
-    CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, floor_rel * floor_rel, m->stream));
+    // FP32 pass 1 leaves weights uncertain by ~8 eps W: those within 16 eps W
+    // of the cut may still cross it, and kept weights below 256 eps W are not
+    // resolved relative to their own size (refinement pass classes)
+    const double eps32 = 1.1920928955078125e-07;
+    const double band = f64 ? 0.0 : 16.0 * eps32, resolved = f64 ? 0.0 : 256.0 * eps32;
+    CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, band, resolved, floor_rel * floor_rel,
+                           m->stream));
   }
   // results land at the level-local index a (h_res[16 a .. 16 a + 15])
   if (L.act.size() > m->h_res_cap) return fail(CTEBD_ERR_ARG, "too many clusters");
@@ -1080,18 +1090,57 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
   // column's own weight) with relative thresholds only, and rotate V and Z by
   // the result.  Rotations below 32 eps sqrt(a d) are skipped: the weight they
   // could move is below n (32 eps)^2 of the total.
+  //
+  // The kept weight is a sum over the kept set and the tail a sum over the
+  // discarded set, so rotations within either set change neither.  With the
+  // columns sorted by their pass-1 weight, pairs of surely discarded
+  // directions are skipped, and so are pairs of kept directions whose weights
+  // pass 1 already resolved (their Rayleigh quotients are accurate to second
+  // order); block pairs entirely in one such class are skipped outright.
   std::vector<int> ref;
   for (int a : sel)   // nothing to refine where every direction is kept
     if ((int)m->h_res[16 * a] < L.ne[a]) ref.push_back(a);
   if (ref.empty()) return CTEBD_OK;
   std::vector<const void*> Z2;
-  std::vector<void*> accW;
-  for (int a : ref) {
-    Z2.push_back(ws[L.act[a]].bufB);
-    accW.push_back(ws[L.act[a]].W);
-  }
+  for (int a : ref) Z2.push_back(ws[L.act[a]].bufB);
   TRY(level_gram(m, ws, L, ref, Z2));
-  TRY(level_eig(m, ws, L, ref, accW, 1e-12, 32.0, L.sw2));
+  {
+    // Gram rows / columns and V columns into descending pass-1 order
+    std::vector<PermProb> pg, pv;
+    long long mg = 0, mv = 0;
+    for (int a : ref) {
+      Work& w = ws[L.act[a]];
+      PermProb g{};
+      g.src = w.G; g.dst = w.W; g.perm = w.perm; g.rows = L.nepad[a]; g.cols = L.ne[a];
+      g.lds = L.nepad[a]; g.ldd = L.nepad[a]; g.mode = 1;
+      pg.push_back(g);
+      mg = std::max(mg, (long long)L.nepad[a] * L.nepad[a]);
+      PermProb v{};
+      v.src = w.V; v.dst = w.G; v.perm = w.perm; v.rows = L.nn[a]; v.cols = L.ne[a];
+      v.lds = L.vld[a]; v.ldd = L.vld[a]; v.mode = 0;
+      pv.push_back(v);
+      mv = std::max(mv, (long long)L.nn[a] * L.ne[a]);
+    }
+    const PermProb *dpg, *dpv;
+    TRY(m->stage.push(pg.data(), pg.size(), &dpg));
+    TRY(m->stage.push(pv.data(), pv.size(), &dpv));
+    ProfScope ps(m->prof, m->stream, KK_GATHER, 0, 0);
+    // sorted Gram -> W; the raw Gram (G) is then free for the sorted V
+    CUDA_TRY(f64 ? launch_permute<double>(dpg, (int)pg.size(), mg, m->stream)
+                 : launch_permute<float>(dpg, (int)pg.size(), mg, m->stream));
+    CUDA_TRY(f64 ? launch_permute<double>(dpv, (int)pv.size(), mv, m->stream)
+                 : launch_permute<float>(dpv, (int)pv.size(), mv, m->stream));
+    for (int a : ref) {
+      Work& w = ws[L.act[a]];
+      void* gram = w.W;   // sorted Gram
+      w.W = w.V;          // old V: free, the pass-2 accumulator
+      w.V = w.G;          // sorted V
+      w.G = gram;
+    }
+  }
+  std::vector<void*> accW;
+  for (int a : ref) accW.push_back(ws[L.act[a]].W);
+  TRY(level_eig(m, ws, L, ref, accW, 1e-12, 32.0, L.sw2, true));
   std::vector<GemmProb> probs;
   for (int a : ref) {
     Work& w = ws[L.act[a]];

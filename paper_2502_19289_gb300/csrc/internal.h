@@ -44,6 +44,9 @@ struct EigProb {
   double floor_factor; // absolute rotation floor = eps * trace * floor_factor
   int* jflag;          // per pair slot: 1 when its J_p is not the identity; null: always apply
   double rel_skip;     // relative rotation floor in units of eps (0: 4)
+  int cut_lo, cut_hi;  // cut_hi > 0: columns sorted by weight, [0, cut_lo) kept and
+                       // [cut_hi, npad) discarded for sure; rotations inside either
+                       // set are skipped (they move no weight across the cut)
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -52,9 +55,23 @@ struct SelProb {
   int n;
   int* perm;           // out: kept column indices, descending rho
   double* lam_out;     // out: renormalised kept spectrum (fp64)
-  double* res;         // out: [0] r, [1] f, [2] W, [3] kept, [4] rank before chi_max cap
+  double* res;         // out: [0] r, [1] f, [2] W, [3] kept, [4] rank before chi_max cap,
+                       // [5] weight inside the n directions, [6] first index whose weight
+                       // is within band * W of the smallest kept weight or below
+                       // resolved * W, [7] first index below that band; perm receives
+                       // the full descending order
   const double* W_ext; // optional total weight ||M||_F^2 (sketched split): the
                        // weight outside the n directions counts as discarded
+};
+
+// Column permutation (mode 0: dst[r][c] = src[r][perm[c]], r < rows, c < cols)
+// or symmetric permutation of a padded square matrix (mode 1: dst[i][j] =
+// src[perm[i]][perm[j]] for i, j < cols, zero elsewhere up to rows = npad).
+struct PermProb {
+  const void* src;
+  void* dst;
+  const int* perm;
+  int rows, cols, lds, ldd, mode;
 };
 
 struct RowScaleProb {   // X[r][c] *= lam[r >> shift]
@@ -126,8 +143,10 @@ cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const i
                                  cudaStream_t s);
 cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, const int* d_n, int n_probs,
                                  int max_n, cudaStream_t s);
-cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff,
-                          double floor2, cudaStream_t s);
+template <typename R>
+cudaError_t launch_permute(const PermProb* d_probs, int n_probs, long long max_elems, cudaStream_t s);
+cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff, double band,
+                          double resolved, double floor2, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gather(const GatherProb* d_probs, int n_probs, long long max_elems,
                           cudaStream_t s);

@@ -207,6 +207,12 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
   __shared__ int nrot, nsig;
   int I, J;
   circle(round, blockIdx.x, P.nb, I, J);
+  const bool cut = P.cut_hi > 0 && P.jflag;
+  if (cut && (((I + 1) * JB <= P.cut_lo && (J + 1) * JB <= P.cut_lo) ||
+              (I * JB >= P.cut_hi && J * JB >= P.cut_hi))) {
+    if (threadIdx.x == 0) P.jflag[blockIdx.x] = 0;   // both blocks on one side of the cut
+    return;
+  }
   const CT* G = (const CT*)P.G;
   for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
     const int li = e / D, lj = e % D;
@@ -232,6 +238,13 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
         R c, s; CT e; bool skip, sig;
         jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip,
                        sig);
+        if (cut) {
+          const int gp = p < JB ? I * JB + p : J * JB + p - JB;
+          const int gq = q < JB ? I * JB + q : J * JB + q - JB;
+          if ((gp < P.cut_lo && gq < P.cut_lo) || (gp >= P.cut_hi && gq >= P.cut_hi)) {
+            skip = true; sig = false; c = 1; s = 0; e = cmk<CT>(1, 0);
+          }
+        }
         tu[threadIdx.x] = s / ((R)1 + c); sn[threadIdx.x] = s; ph[threadIdx.x] = e;
         if (!skip) atomicAdd(&nrot, 1);
         if (sig) atomicAdd(&nsig, 1);
@@ -569,7 +582,8 @@ cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, cons
 constexpr int SEL_MAX = 4096;
 
 __global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ probs, int chi_max,
-                                                 double cutoff, double floor2) {
+                                                 double cutoff, double band, double resolved,
+                                                 double floor2) {
   extern __shared__ unsigned char smraw[];
   double* key = reinterpret_cast<double*>(smraw);
   int* idx = reinterpret_cast<int*>(key + SEL_MAX);
@@ -630,18 +644,26 @@ __global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ pro
     P.res[1] = W > 0 ? kept / W : 1.0;
     P.res[2] = W;
     P.res[3] = kept;
+    // directions whose weight is within band * W of the smallest kept one
+    // may still cross the cut: [lo, hi) in the sorted order; kept directions
+    // below resolved * W are not resolved by the first pass either
+    const double cut = key[r - 1], d = band * W;
+    int lo = 0, hi = 0;
+    while (lo < n && key[lo] > fmax(cut + d, resolved * W)) lo++;
+    while (hi < n && key[hi] >= cut - d) hi++;
+    P.res[6] = lo;
+    P.res[7] = hi;
   }
   __syncthreads();
   const int r = r_s;
   const double kept = kept_s;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    P.perm[i] = idx[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) P.perm[i] = idx[i];
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
     P.lam_out[i] = kept > 0 ? sqrt(fmax(key[i], 0.0) / kept) : 0.0;
-  }
 }
 
-cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff,
-                          double floor2, cudaStream_t s) {
+cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff, double band,
+                          double resolved, double floor2, cudaStream_t s) {
   if (n_probs <= 0) return cudaSuccess;
   const size_t sm = SEL_MAX * (sizeof(double) + sizeof(int));
   static bool attr = false;
@@ -649,7 +671,7 @@ cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, doub
     cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  k_select<<<n_probs, 1024, sm, s>>>(d_probs, chi_max, cutoff, floor2);
+  k_select<<<n_probs, 1024, sm, s>>>(d_probs, chi_max, cutoff, band, resolved, floor2);
   return cudaGetLastError();
 }
 
@@ -691,6 +713,39 @@ cudaError_t launch_gather(const GatherProb* d_probs, int n_probs, long long max_
 }
 template cudaError_t launch_gather<float>(const GatherProb*, int, long long, cudaStream_t);
 template cudaError_t launch_gather<double>(const GatherProb*, int, long long, cudaStream_t);
+
+template <typename R>
+__global__ void k_permute(const PermProb* __restrict__ probs) {
+  using CT = typename C2<R>::T;
+  const PermProb P = probs[blockIdx.y];
+  const CT* src = (const CT*)P.src;
+  CT* dst = (CT*)P.dst;
+  const long long tot = (long long)P.rows * (P.mode == 0 ? P.cols : P.rows);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (P.mode == 0) {
+      const long long r = e / P.cols;
+      const int c = (int)(e % P.cols);
+      dst[r * P.ldd + c] = src[r * P.lds + P.perm[c]];
+    } else {
+      const int i = (int)(e / P.rows), j = (int)(e % P.rows);
+      dst[(long long)i * P.ldd + j] = (i < P.cols && j < P.cols)
+                                          ? src[(long long)P.perm[i] * P.lds + P.perm[j]]
+                                          : cmk<CT>(0, 0);
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_permute(const PermProb* d_probs, int n_probs, long long max_elems, cudaStream_t s) {
+  if (n_probs <= 0 || max_elems <= 0) return cudaSuccess;
+  long long gx = (max_elems + 255) / 256;
+  if (gx > 65535) gx = 65535;
+  k_permute<R><<<dim3((unsigned)gx, n_probs), 256, 0, s>>>(d_probs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_permute<float>(const PermProb*, int, long long, cudaStream_t);
+template cudaError_t launch_permute<double>(const PermProb*, int, long long, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // One-qubit gates on singleton sites, amplitudes, conversions.

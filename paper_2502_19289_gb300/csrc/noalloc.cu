@@ -213,7 +213,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     sp.lam_out = lam_out; sp.res = (double*)(S + NA_OFF_RES);
     const SelProb* dsp;
     if (int rc = d.put(&sp, 1, &dsp)) return rc;
-    NA_CUDA(launch_select(dsp, 1, chi_max, cutoff, 1e-12, s));
+    NA_CUDA(launch_select(dsp, 1, chi_max, cutoff, 0.0, 0.0, 1e-12, s));
     NA_CUDA(cudaMemcpyAsync(res, S + NA_OFF_RES, sizeof(res), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
     d.off = 0;
