@@ -410,6 +410,156 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
   }
 }
 
+// FP32 apply, one 64 x 64 complex tile per CTA of 128 threads.  Each thread
+// owns 8 rows x 4 columns of the tile: rows 16 w + rg + 2 i (warp w, half-warp
+// rg, i < 8) and columns 4 cg .. 4 cg + 3 (cg = lane mod 16), so a k step
+// reads 8 broadcast values of the left operand and two 16-byte vectors of the
+// right one for 32 complex FMAs.  Tiles arrive by 16-byte cp.async copies
+// into rows padded to 66 elements (16-byte aligned, and the two half-warps'
+// rows fall in different banks); J_P is fetched while T is written back.
+namespace {
+constexpr int AP_D = 64, AP_LD = 66, AP_THREADS = 128;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+}  // namespace
+
+__global__ void __launch_bounds__(AP_THREADS, 3) k_eig_apply_f32(const EigProb* __restrict__ probs, int round) {
+  constexpr int JB = 32, D = AP_D, LD = AP_LD;
+  const EigProb P = probs[blockIdx.y];
+  if (!P.active || round >= P.nb - 1) return;
+  const int h = P.nb / 2, nG = h * (h + 1) / 2, nV = h * h;
+  const int tile = blockIdx.x;
+  if (tile >= nG + nV) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* S0 = reinterpret_cast<float2*>(smraw);
+  float2* S1 = S0 + D * LD;
+  const bool isG = tile < nG;
+  int Pp, Qp;
+  if (isG) {
+    int t = tile, row = 0;
+    while (t >= h - row) { t -= h - row; row++; }
+    Pp = row;
+    Qp = row + t;
+  } else {
+    Pp = (tile - nG) / h;
+    Qp = (tile - nG) % h;
+  }
+  const bool fq = !P.jflag || P.jflag[Qp], fp = isG && (!P.jflag || P.jflag[Pp]);
+  if (!fq && !fp) return;
+  if (P.jflag && threadIdx.x == 0)
+    atomicAdd(P.off + 2, 8.0 * D * D * D * ((fq ? 1 : 0) + (fp ? 1 : 0)));
+  int K1, K2, I1 = 0, I2 = 0;
+  circle(round, Qp, P.nb, K1, K2);
+  if (isG) circle(round, Pp, P.nb, I1, I2);
+  float2* X = reinterpret_cast<float2*>(isG ? P.G : P.V);
+  const float2* Jb = reinterpret_cast<const float2*>(P.J);
+  const long long np = P.npad;
+  auto grow = [&](int li) -> long long {
+    if (!isG) return (long long)Pp * D + li;
+    return li < JB ? (long long)I1 * JB + li : (long long)I2 * JB + li - JB;
+  };
+  auto gcol = [&](int lj) -> long long {
+    return lj < JB ? (long long)K1 * JB + lj : (long long)K2 * JB + lj - JB;
+  };
+  const int t = threadIdx.x;
+  for (int c = t; c < D * (D / 2); c += AP_THREADS) {   // 16-byte chunks: 2 complex
+    const int li = c >> 5, lj = (c & 31) * 2;
+    cp_async16(S0 + li * LD + lj, X + grow(li) * np + gcol(lj));
+    if (fq) cp_async16(S1 + li * LD + lj, Jb + (long long)Qp * D * D + li * D + lj);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int w = t >> 5, lane = t & 31, rg = lane >> 4, cg = lane & 15;
+  const int r0 = 16 * w + rg, c0 = 4 * cg;
+  float2 acc[8][4];
+  if (fq) {
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int k = 0; k < D; k++) {            // T = X_tile J_Q
+      float2 a[8], b[4];
+#pragma unroll
+      for (int i = 0; i < 8; i++) a[i] = S0[(r0 + 2 * i) * LD + k];
+      const float4 b01 = *reinterpret_cast<const float4*>(S1 + k * LD + c0);
+      const float4 b23 = *reinterpret_cast<const float4*>(S1 + k * LD + c0 + 2);
+      b[0] = make_float2(b01.x, b01.y); b[1] = make_float2(b01.z, b01.w);
+      b[2] = make_float2(b23.x, b23.y); b[3] = make_float2(b23.z, b23.w);
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[i][j] = S0[(r0 + 2 * i) * LD + c0 + j];
+  }
+  if (isG) {
+    __syncthreads();                           // every read of S0 and S1 is done
+    if (fp) {
+      for (int c = t; c < D * (D / 2); c += AP_THREADS) {
+        const int li = c >> 5, lj = (c & 31) * 2;
+        cp_async16(S1 + li * LD + lj, Jb + (long long)Pp * D * D + li * D + lj);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {              // T -> S0
+      float4* dst = reinterpret_cast<float4*>(S0 + (r0 + 2 * i) * LD + c0);
+      dst[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+      dst[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (fp) {
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int k = 0; k < D; k++) {          // Y = J_P^H T
+        float2 a[8], b[4];
+#pragma unroll
+        for (int i = 0; i < 8; i++) a[i] = cconj(S1[k * LD + r0 + 2 * i]);
+        const float4 b01 = *reinterpret_cast<const float4*>(S0 + k * LD + c0);
+        const float4 b23 = *reinterpret_cast<const float4*>(S0 + k * LD + c0 + 2);
+        b[0] = make_float2(b01.x, b01.y); b[1] = make_float2(b01.z, b01.w);
+        b[2] = make_float2(b23.x, b23.y); b[3] = make_float2(b23.z, b23.w);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++) {                // the tile, 32 bytes per thread and row
+    float4* dst = reinterpret_cast<float4*>(X + grow(r0 + 2 * i) * np + gcol(c0));
+    dst[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+    dst[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+  }
+  if (isG && Pp != Qp) {                       // Hermitian mirror tile (Q, P), row by row
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) S0[(r0 + 2 * i) * LD + c0 + j] = acc[i][j];
+    __syncthreads();
+    for (int e = t; e < D * D; e += AP_THREADS) {
+      const int li = e / D, lj = e % D;
+      X[gcol(li) * np + grow(lj)] = cconj(S0[lj * LD + li]);
+    }
+  }
+}
+
 template <typename R>
 __global__ void k_eig_init(const EigProb* __restrict__ probs, int max_npad) {
   using CT = typename C2<R>::T;
@@ -488,9 +638,20 @@ cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, in
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
   eig_attrs<R>();
-  const size_t sm_apply = 2 * sizeof(CT) * D * LD;
   const int h = max_nb / 2;
-  k_eig_apply<R><<<dim3(h * (h + 1) / 2 + h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
+  if constexpr (sizeof(R) == 4) {
+    static_assert(D == AP_D, "FP32 apply tile");
+    const size_t sm = 2 * sizeof(float2) * AP_D * AP_LD;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_eig_apply_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_eig_apply_f32<<<dim3(h * (h + 1) / 2 + h * h, n_probs), AP_THREADS, sm, s>>>(d_probs, round);
+  } else {
+    const size_t sm_apply = 2 * sizeof(CT) * D * LD;
+    k_eig_apply<R><<<dim3(h * (h + 1) / 2 + h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
+  }
   return cudaGetLastError();
 }
 
