@@ -758,6 +758,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     eps[i].jflag = d_flag + (size_t)i * maxh;
     eps[i].rel_skip = rel_skip;
     if (use_cut) {   // columns sorted by the previous pass: [lo, hi) around the cut
+      eps[i].move_rel = 1e-13;
       eps[i].cut_lo = (int)m->h_res[16 * a + 6];
       eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
     }
@@ -887,11 +888,13 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
   TRY(m->stage.push(sp.data(), na, &dsp));
   {
     ProfScope pss(m->prof, m->stream, KK_SELECT, 0, 0);
-    // FP32 pass 1 leaves weights uncertain by ~8 eps W: those within 16 eps W
-    // of the cut may still cross it, and kept weights below 256 eps W are not
-    // resolved relative to their own size (refinement pass classes)
+    // FP32 pass 1 leaves couplings of up to ~8 eps W: weights within 16 eps W
+    // of the cut may still cross it, and kept weights below 1024 eps W are not
+    // resolved relative to their own size -- their second-order error
+    // (8 eps W)^2 / gap reaches 1e-3 of the weight on spectra whose neighbours
+    // are a few per cent apart (refinement pass classes)
     const double eps32 = 1.1920928955078125e-07;
-    const double band = f64 ? 0.0 : 16.0 * eps32, resolved = f64 ? 0.0 : 256.0 * eps32;
+    const double band = f64 ? 0.0 : 16.0 * eps32, resolved = f64 ? 0.0 : 1024.0 * eps32;
     CUDA_TRY(launch_select(dsp, na, m->cfg.chi_max, m->cfg.cutoff, band, resolved, floor_rel * floor_rel,
                            m->stream));
   }
@@ -1089,14 +1092,19 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
   // Gram of the rotated columns Z = M V (whose rounding is relative to each
   // column's own weight) with relative thresholds only, and rotate V and Z by
   // the result.  Rotations below 32 eps sqrt(a d) are skipped: the weight they
-  // could move is below n (32 eps)^2 of the total.
+  // could move is below n (32 eps)^2 of the total.  A rotation keeps the
+  // sweeps going only if it moves more than 1e-13 of the total weight: among
+  // directions whose weights sit at the rounding level the relative test
+  // alone never settles, and what such rotations leave unmoved is below
+  // n^2 / 2 * 1e-13 of the total.
   //
   // The kept weight is a sum over the kept set and the tail a sum over the
   // discarded set, so rotations within either set change neither.  With the
   // columns sorted by their pass-1 weight, pairs of surely discarded
   // directions are skipped, and so are pairs of kept directions whose weights
-  // pass 1 already resolved (their Rayleigh quotients are accurate to second
-  // order); block pairs entirely in one such class are skipped outright.
+  // pass 1 already resolved (>= 1024 eps W: their Rayleigh quotients are
+  // accurate to second order); block pairs entirely in one such class are
+  // skipped outright.
   std::vector<int> ref;
   for (int a : sel)   // nothing to refine where every direction is kept
     if ((int)m->h_res[16 * a] < L.ne[a]) ref.push_back(a);

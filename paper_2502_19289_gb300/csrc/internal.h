@@ -44,6 +44,8 @@ struct EigProb {
   double floor_factor; // absolute rotation floor = eps * trace * floor_factor
   int* jflag;          // per pair slot: 1 when its J_p is not the identity; null: always apply
   double rel_skip;     // relative rotation floor in units of eps (0: 4)
+  double move_rel;     // > 0: a rotation keeps the sweeps going only if it moves more
+                       // than move_rel * trace of weight between its two directions
   int cut_lo, cut_hi;  // cut_hi > 0: columns sorted by weight, [0, cut_lo) kept and
                        // [cut_hi, npad) discarded for sure; rotations inside either
                        // set are skipped (they move no weight across the cut)

@@ -193,7 +193,7 @@ __device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R flo
 template <typename R>
 __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ probs, int round) {
   using CT = typename C2<R>::T;
-  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
+  constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, NBLK = JB * (JB + 1) / 2;
   const EigProb P = probs[blockIdx.y];
   if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2) return;
   extern __shared__ unsigned char smraw[];
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
   CT* ph = reinterpret_cast<CT*>(sn + JB);
   int* pp = reinterpret_cast<int*>(ph + JB);
   int* pq = pp + JB;
+  unsigned short* blk = reinterpret_cast<unsigned short*>(pq + JB);   // pair blocks a <= b: a | b << 8
   __shared__ int nrot, nsig;
   int I, J;
   circle(round, blockIdx.x, P.nb, I, J);
@@ -221,9 +222,15 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
     A[li * LD + lj] = G[gi * P.npad + gj];
     Q[li * LD + lj] = cmk<CT>(li == lj ? 1 : 0, 0);
   }
+  for (int e = threadIdx.x; e < NBLK; e += blockDim.x) {
+    int a = 0, t = e;
+    while (t >= JB - a) { t -= JB - a; a++; }
+    blk[e] = (unsigned short)(a | ((a + t) << 8));
+  }
   const R eps_r = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
   const R floor_abs = (R)((double)eps_r * (*P.scale) * P.floor_factor);
   const R rel_skip = P.rel_skip > 0 ? (R)P.rel_skip : (R)4;
+  const R move_abs = (R)(P.move_rel * (*P.scale));
   __syncthreads();
   int total = 0, total_sig = 0;
   const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
@@ -238,6 +245,10 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
         R c, s; CT e; bool skip, sig;
         jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip,
                        sig);
+        if (sig && move_abs > 0) {   // the rotation moves |t g| of weight between p and q (t = s / c)
+          const CT g = A[p * LD + q];
+          if (!(fabs(s) * sqrt(g.x * g.x + g.y * g.y) > move_abs * c)) sig = false;
+        }
         if (cut) {
           const int gp = p < JB ? I * JB + p : J * JB + p - JB;
           const int gq = q < JB ? I * JB + q : J * JB + q - JB;
@@ -250,31 +261,45 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
         if (sig) atomicAdd(&nsig, 1);
       }
       __syncthreads();
-      // x' = c x - s y, y' = s x + c y in Rutishauser's form
+      // A <- R^H A R and Q <- Q R, every rotation in Rutishauser's form
       //   x' = x - s (y + tau x),  y' = y + s (x - tau y),  tau = s / (1 + c):
       // for small angles c = 1 - s tau is not rounded to 1, which would grow
-      // every vector by (1 + t^2) per rotation in FP32
-      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of A and Q
+      // every vector by (1 + t^2) per rotation in FP32.  The rotations of a
+      // round act on disjoint pairs, so the 2 x 2 block of A on pairs (a, b)
+      // becomes R_a^H B R_b by itself: one thread per block with a <= b, the
+      // block below the diagonal is its conjugate transpose (A stays Hermitian).
+      for (int e = threadIdx.x; e < NBLK; e += blockDim.x) {
+        const int a = blk[e] & 0xff, b = blk[e] >> 8;
+        const int pa = pp[a], qa = pq[a], pb = pp[b], qb = pq[b];
+        const CT x00 = A[pa * LD + pb], x10 = A[qa * LD + pb];
+        const R tb = tu[b], sb = sn[b];
+        const CT fb = ph[b];
+        const CT y0 = cmul(A[pa * LD + qb], fb), y1 = cmul(A[qa * LD + qb], fb);
+        const CT n00 = cmk<CT>(x00.x - sb * (y0.x + tb * x00.x), x00.y - sb * (y0.y + tb * x00.y));
+        const CT n01 = cmk<CT>(y0.x + sb * (x00.x - tb * y0.x), y0.y + sb * (x00.y - tb * y0.y));
+        const CT n10 = cmk<CT>(x10.x - sb * (y1.x + tb * x10.x), x10.y - sb * (y1.y + tb * x10.y));
+        const CT n11 = cmk<CT>(y1.x + sb * (x10.x - tb * y1.x), y1.y + sb * (x10.y - tb * y1.y));
+        const R ta = tu[a], sa = sn[a];
+        const CT fa = cconj(ph[a]);
+        const CT z0 = cmul(n10, fa), z1 = cmul(n11, fa);
+        const CT m00 = cmk<CT>(n00.x - sa * (z0.x + ta * n00.x), n00.y - sa * (z0.y + ta * n00.y));
+        const CT m10 = cmk<CT>(z0.x + sa * (n00.x - ta * z0.x), z0.y + sa * (n00.y - ta * z0.y));
+        const CT m01 = cmk<CT>(n01.x - sa * (z1.x + ta * n01.x), n01.y - sa * (z1.y + ta * n01.y));
+        const CT m11 = cmk<CT>(z1.x + sa * (n01.x - ta * z1.x), z1.y + sa * (n01.y - ta * z1.y));
+        A[pa * LD + pb] = m00; A[pa * LD + qb] = m01;
+        A[qa * LD + pb] = m10; A[qa * LD + qb] = m11;
+        if (a != b) {
+          A[pb * LD + pa] = cconj(m00); A[qb * LD + pa] = cconj(m01);
+          A[pb * LD + qa] = cconj(m10); A[qb * LD + qa] = cconj(m11);
+        }
+      }
+      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of Q
         const int row = e / JB, k = e % JB;
         const int p = pp[k], q = pq[k];
         const R t = tu[k], s = sn[k];
-        const CT f = ph[k];
-        CT x = A[row * LD + p], y = cmul(A[row * LD + q], f);
-        A[row * LD + p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
-        A[row * LD + q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
-        x = Q[row * LD + p]; y = cmul(Q[row * LD + q], f);
+        const CT x = Q[row * LD + p], y = cmul(Q[row * LD + q], ph[k]);
         Q[row * LD + p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
         Q[row * LD + q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // rows of A
-        const int col = e / JB, k = e % JB;
-        const int p = pp[k], q = pq[k];
-        const R t = tu[k], s = sn[k];
-        const CT f = cconj(ph[k]);
-        CT x = A[p * LD + col], y = cmul(A[q * LD + col], f);
-        A[p * LD + col] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
-        A[q * LD + col] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
       }
       __syncthreads();
     }
@@ -616,7 +641,8 @@ static void eig_attrs() {
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
   static bool attr = false;
   if (attr) return;
-  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int));
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
+                          sizeof(unsigned short) * JB * (JB + 1) / 2;
   const size_t sm_apply = 2 * sizeof(CT) * D * LD;
   cudaFuncSetAttribute(k_eig_inner<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
   cudaFuncSetAttribute(k_eig_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
@@ -628,7 +654,8 @@ cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, in
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
   eig_attrs<R>();
-  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int));
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
+                          sizeof(unsigned short) * JB * (JB + 1) / 2;
   k_eig_inner<R><<<dim3(max_nb / 2, n_probs), 256, sm_inner, s>>>(d_probs, round);
   return cudaGetLastError();
 }
