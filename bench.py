@@ -323,6 +323,101 @@ def cpu_baseline(seconds=15.0, chi=128, nsites=16):
             "extrapolated_chi1024": v * (chi / 1024.0) ** 3}
 
 
+def run_cfg2(args):
+    """Sketched split (randomized range finder + CholeskyQR + Rayleigh-Ritz, with
+    the tail check) against the full split on the cfg2 workload: n=100, 50
+    layers of random-structured Clifford+T (10% T, 10% long-range pairs),
+    chi_max=256, cutoff 1e-10, k_max=6, from |0...0> through the whole circuit.
+    Three modes: full split; sketch sized by the Eq. 9 bound; sketch sized by
+    the learned rank predictor (trained here on cfg2-shaped circuits of 40
+    qubits).  Device time of the cluster updates (CUDA events on the library's
+    stream); the modes must agree on log F and the bond dimensions."""
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import paper_2502_19289_gb300.rank_model as R
+    import synth
+    w = synth.WORKLOADS[2]
+    if args.layers:   # same gate statistics, deeper circuit (bonds grow towards chi_max)
+        w = synth.reduced(2, w.n_qubits, args.layers)
+    n, chi, over = w.n_qubits, w.chi_max, 8
+    q_max = w.k_max + 2 * int(math.log2(chi))
+    c = w.circuit(0, 2)
+    stream = torch.cuda.Stream()
+
+    t0 = time.perf_counter()
+    small = synth.reduced(2, 40, 60)
+    Xs, rs, bs = [], [], []
+    for seed in range(1, 7):
+        cc = small.circuit(seed, 2)
+        X, r, b = R.collect((cc.gates, cc.params), small.n_qubits, chi, w.cutoff, q_max, w.k_max,
+                            stream.cuda_stream)
+        Xs.append(X); rs.append(r); bs.append(b)
+    X, r, b = np.concatenate(Xs), np.concatenate(rs), np.concatenate(bs)
+    params, hist = R.train(X, R.bucket_of(r, b), epochs=150, lr=3e-3, batch=256, seed=0)
+    train_s = time.perf_counter() - t0
+
+    def run(oversample, learned):
+        circ = P.Circuit(n, c.gates, c.params)
+        cfg = P.make_config(n, chi, w.cutoff, q_max, 0, w.k_max, P.FP32, sketch_oversample=oversample)
+        mps = P.MPS(cfg, stream.cuda_stream)
+        hint = R.make_hint_fn(mps, circ, cfg, params) if learned else None
+        start, updates, dev_ms, work, splits = 0, 0, 0.0, 0.0, 0
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        while start < circ.n_layers:
+            chi_now = mps.bond_dims()
+            clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, start, chi_now, cfg)
+            if oversample > 0 and clusters:
+                hints = (hint(clusters, chi_now) if hint else
+                         [P.cluster_rank_bounds(circ.gates, circ.n_gates, cl, chi_now) for cl in clusters])
+                for cl, h in zip(clusters, hints):
+                    for j, v in enumerate(h[:11]):
+                        cl.rank_hint[j] = int(v)
+            mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)
+            if clusters:
+                Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in clusters]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mps.step(clusters, Us)
+                e1.record(stream)
+                e1.synchronize()
+                dev_ms += e0.elapsed_time(e1)
+                updates += len(clusters)
+                log = mps.split_log()
+                work += float(np.sum(log[:, 9] ** 3))
+                splits += len(log)
+            start = stop
+        wall = time.perf_counter() - w0
+        sk, fb = mps.sketch_stats()
+        out = {"updates_per_s": updates / (dev_ms / 1000.0), "e2e_updates_per_s": updates / wall,
+               "updates": updates, "device_s": dev_ms / 1000.0, "logF": float(math.log(mps.fidelity())),
+               "splits": splits, "sketched": sk, "fell_back": fb, "eigen_work_sum_ne3": work,
+               "max_chi": int(max(mps.bond_dims()))}
+        dims = list(mps.bond_dims())
+        mps.close()
+        return out, dims
+
+    full, d_full = run(0, False)
+    eq9, d_eq9 = run(over, False)
+    learned, d_l = run(over, True)
+    line = {"metric": "cluster updates/s, cfg2 workload: full split vs sketched split (Eq. 9 and learned sizes)",
+            "unit": "cluster updates/s", "higher_is_better": True, "n_gpus": 1, "dtype": "c64",
+            "data": "synthetic (seeded circuit from |0...0>)",
+            "config": {"workload": f"cfg2: n=100, {w.n_layers}-layer random-structured Clifford+T (10% T, 10% "
+                                   "long-range pairs), chi_max=256, cutoff 1e-10, k_max=6, Q_max=22, sketch "
+                                   "oversampling 8",
+                       "rank_model": f"trained on 6 cfg2-shaped circuits (n=40, 60 layers), {len(X)} splits, "
+                                     f"loss {hist[0]:.3f} -> {hist[-1]:.3f}, {train_s:.1f} s"},
+            "modes": {"full": full, "sketch_eq9": eq9, "sketch_learned": learned},
+            "speedup_eq9": eq9["updates_per_s"] / full["updates_per_s"],
+            "speedup_learned": learned["updates_per_s"] / full["updates_per_s"],
+            "agreement": {"max_abs_dlogF": max(abs(eq9["logF"] - full["logF"]),
+                                              abs(learned["logF"] - full["logF"])),
+                          "bond_dims_equal": d_full == d_eq9 == d_l}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,7 +428,13 @@ def main():
     ap.add_argument("--chi", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2"],
+                    help="cfg4: the headline (saturated chi=1024, full split); cfg2: full vs sketched split")
+    ap.add_argument("--layers", type=int, default=0, help="cfg2 mode: circuit depth (default: the workload's 50)")
     args = ap.parse_args()
+    if args.workload == "cfg2":
+        run_cfg2(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
