@@ -263,6 +263,14 @@ int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* s
    work, 2 always.  FP64 GEMMs always use the CUDA cores. */
 int ctebd_set_tensor_cores(int mode);
 
+/* Eigen-solve sweep loop on the device (not in the paper): with per-launch
+   profiling off, each batched eigen-solve runs as one CUDA graph whose WHILE
+   node repeats a sweep until every problem has converged (or 30 sweeps), with
+   no host round trip per sweep.  on = 1 (default) uses it, 0 launches every
+   round from the host.  Process-wide; results are the same either way.
+   Returns CTEBD_ERR_ARG for other values. */
+int ctebd_set_sweep_graphs(int on);
+
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0
    stops timing; launch counts and algorithmic flop/byte counts are always

@@ -83,6 +83,7 @@ def _load():
         "mlp_nparams_abi": [],
         "tc_cgemm": [P, P, P, I, I, I, P],
         "ctebd_set_tensor_cores": [I],
+        "ctebd_set_sweep_graphs": [I],
         "mlp_forward": [P, P, I, P, P],
         "mlp_loss_grad": [P, P, P, I, P, P, P],
         "mlp_adam": [P, P, P, P, I, C.c_float, I, P],
@@ -174,6 +175,12 @@ def rank_features(gates, n_gates, cl: Cluster, chi, entropy, cfg: Config) -> np.
 def set_tensor_cores(mode: int):
     """FP32 GEMM policy: 0 CUDA cores only, 1 above 2 GFLOP (default), 2 always."""
     _check(_lib.ctebd_set_tensor_cores(int(mode)), "ctebd_set_tensor_cores")
+
+
+def set_sweep_graphs(on: bool):
+    """Run each eigen-solve's sweep loop on the device as one CUDA graph (default)
+    or launch every round from the host; process-wide (ctebd_set_sweep_graphs)."""
+    _check(_lib.ctebd_set_sweep_graphs(int(bool(on))), "ctebd_set_sweep_graphs")
 
 
 def tc_cgemm(A_ptr, B_ptr, C_ptr, M, K, N, stream=None):

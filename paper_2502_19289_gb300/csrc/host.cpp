@@ -728,6 +728,66 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // into acc[i] (set to identity first).  floor_factor scales the absolute
 // rotation floor eps * trace(G): 1 for a Gram computed from Mbar (absolute
 // rounding), ~0 for a Gram of already rotated columns (relative accuracy).
+// ---------------------------------------------------------------------------
+// Device-side sweep loop: one CUDA graph with a WHILE conditional node whose
+// body is the rounds of one sweep (inner + apply per round) followed by the
+// sweep-end kernel, which folds the counters, retires converged problems and
+// sets the loop condition.  One launch and one host read per eigen-solve
+// instead of a host round trip per sweep.  Used when per-launch profiling is
+// off (ctebd_set_sweep_graphs; process-wide).
+// ---------------------------------------------------------------------------
+static int g_sweep_graphs = 1;
+
+extern "C" int ctebd_set_sweep_graphs(int on) {
+  if (on < 0 || on > 1) return fail(CTEBD_ERR_ARG, "ctebd_set_sweep_graphs: 0 or 1");
+  g_sweep_graphs = on;
+  return CTEBD_OK;
+}
+
+static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, int max_nb, double* d_cum, int max_sweeps) {
+  const bool f64 = m->fp64;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(m->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = cudaSuccess;
+    for (int t = 0; t < max_nb - 1 && le == cudaSuccess; t++) {
+      le = f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
+               : launch_eig_inner<float>(dep, na, max_nb, t, m->stream);
+      if (le == cudaSuccess)
+        le = f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
+                 : launch_eig_apply<float>(dep, na, max_nb, t, m->stream);
+    }
+    if (le == cudaSuccess) le = launch_sweep_end(dep, na, d_cum, d_cum + 3 * na, max_sweeps, h, m->stream);
+    cudaGraph_t body = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(m->stream, &body);
+    e = le != cudaSuccess ? le : ce;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, m->stream);
+  if (ex) cudaGraphExecDestroy(ex);   // freed once the launch completes
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CTEBD_ERR_CUDA, std::string("sweep graph: ") + cudaGetErrorString(e));
+  }
+  return CTEBD_OK;
+}
+
 static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const std::vector<int>& sel,
                      const std::vector<void*>& acc, double floor_factor, double rel_skip,
                      std::vector<int>& sweeps, bool use_cut = false) {
@@ -771,8 +831,36 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
                  : launch_eig_init<float>(dep, na, max_npad, m->stream));
     CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
   }
-  std::vector<double> hoff(3 * na);
   const int max_sweeps = 30;
+  if (g_sweep_graphs && !m->prof.on) {
+    // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
+    double* d_cum = nullptr;
+    const size_t n_cum = 3 * (size_t)na + 1;
+    CUDA_TRY(cudaMallocAsync(&d_cum, sizeof(double) * n_cum, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
+    CUDA_TRY(eig_prepare(f64));
+    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, max_nb, d_cum, max_sweeps);
+    std::vector<double> hc(n_cum, 0.0);
+    if (rc == CTEBD_OK) {
+      CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cum, sizeof(double) * n_cum, cudaMemcpyDeviceToHost, m->stream));
+      CUDA_TRY(cudaStreamSynchronize(m->stream));
+    }
+    cudaFreeAsync(d_cum, m->stream);
+    cudaFreeAsync(d_off, m->stream);
+    TRY(rc);
+    const double rounds = hc[3 * na] * (max_nb - 1);
+    m->prof.launches[KK_EIG_INNER] += rounds;
+    m->prof.launches[KK_EIG_APPLY] += rounds;
+    for (int i = 0; i < na; i++) {
+      // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
+      m->prof.flops[KK_EIG_INNER] += hc[3 * i] * 42.0 * (2 * JB);
+      m->prof.flops[KK_EIG_APPLY] += hc[3 * i + 1];
+      sweeps[sel[i]] += (int)hc[3 * i + 2];
+    }
+    return CTEBD_OK;
+  }
+  std::vector<double> hoff(3 * na);
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
     double fap_sweep = 0, bap_sweep = 0;

@@ -135,6 +135,16 @@ template <typename R>
 cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round,
                              cudaStream_t s);
 int eig_block(bool fp64);  // JB
+// Set the kernels' shared-memory attributes (idempotent); call before any
+// stream capture of the eigen-solve launches.
+cudaError_t eig_prepare(bool fp64);
+// End of one device-side sweep over n problems (descriptors in device memory,
+// modified in place): add the sweep's counters to cum (3 per problem:
+// rotations, applied flops, sweeps), deactivate converged problems, zero the
+// counters, and let the sweep loop continue while any problem is active and
+// fewer than max_sweeps sweeps ran (count in *n_sweeps).
+cudaError_t launch_sweep_end(EigProb* d_probs, int n, double* cum, double* n_sweeps, int max_sweeps,
+                             cudaGraphConditionalHandle h, cudaStream_t s);
 template <typename R>
 cudaError_t launch_eig_trace(const EigProb* d_probs, int n_probs, cudaStream_t s);
 

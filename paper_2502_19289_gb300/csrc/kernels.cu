@@ -669,16 +669,51 @@ cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, in
   if constexpr (sizeof(R) == 4) {
     static_assert(D == AP_D, "FP32 apply tile");
     const size_t sm = 2 * sizeof(float2) * AP_D * AP_LD;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_eig_apply_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    eig_prepare(false);
     k_eig_apply_f32<<<dim3(h * (h + 1) / 2 + h * h, n_probs), AP_THREADS, sm, s>>>(d_probs, round);
   } else {
     const size_t sm_apply = 2 * sizeof(CT) * D * LD;
     k_eig_apply<R><<<dim3(h * (h + 1) / 2 + h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t eig_prepare(bool fp64) {
+  if (fp64) {
+    eig_attrs<double>();
+  } else {
+    eig_attrs<float>();
+    static bool attr = false;
+    if (!attr) {
+      const size_t sm = 2 * sizeof(float2) * AP_D * AP_LD;
+      cudaFuncSetAttribute(k_eig_apply_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+  }
+  return cudaGetLastError();
+}
+
+// One thread walks the problems (a few hundred at most per batch).
+__global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restrict__ cum,
+                            double* __restrict__ n_sweeps, int max_sweeps, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool any = false;
+  for (int i = 0; i < n; i++) {
+    EigProb& P = probs[i];
+    if (!P.active) continue;
+    cum[3 * i] += P.off[1];
+    cum[3 * i + 1] += P.off[2];
+    cum[3 * i + 2] += 1.0;
+    if (P.off[0] == 0.0) P.active = 0; else any = true;
+    P.off[0] = 0.0; P.off[1] = 0.0; P.off[2] = 0.0;
+  }
+  *n_sweeps += 1.0;
+  cudaGraphSetConditional(h, (any && *n_sweeps < (double)max_sweeps) ? 1u : 0u);
+}
+
+cudaError_t launch_sweep_end(EigProb* d_probs, int n, double* cum, double* n_sweeps, int max_sweeps,
+                             cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_sweep_end<<<1, 32, 0, s>>>(d_probs, n, cum, n_sweeps, max_sweeps, h);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,53 @@
+"""GPU: the eigen-solve sweep loop run on the device (one CUDA graph with a
+WHILE node per batched eigen-solve) against the same sweeps launched round by
+round from the host.  Same kernels in the same order: equal bond dimensions
+and sweep counts, fidelities equal to rounding, and both match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import as_oracle, fidelity_overlap, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(P, c, w, chi, graphs, precision):
+    P.set_sweep_graphs(graphs)
+    try:
+        circ = P.Circuit(c.n_qubits, c.gates, c.params)
+        cfg = P.make_config(c.n_qubits, chi, w.cutoff, w.q_max, 0, w.k_max, precision)
+        mps = P.MPS(cfg)
+        start, logs = 0, []
+        while start < circ.n_layers:
+            clusters, stop, f = P.run_iteration(mps, circ, start)
+            if clusters:
+                logs.append(mps.split_log())
+            start = stop
+        return mps, np.concatenate(logs)
+    finally:
+        P.set_sweep_graphs(True)
+
+
+@pytest.mark.parametrize("precision_name,chi", [("FP32", 32), ("FP32", 256), ("FP64", 32)])
+def test_device_sweeps_match_host_sweeps(precision_name, chi):
+    P = lib()
+    precision = getattr(P, precision_name)
+    w = synth.reduced(2, 20, 110)
+    c = w.circuit(0, 2)
+    m_g, log_g = _run(P, c, w, chi, True, precision)
+    m_h, log_h = _run(P, c, w, chi, False, precision)
+    assert list(m_g.bond_dims()) == list(m_h.bond_dims())
+    np.testing.assert_array_equal(log_g[:, 5], log_h[:, 5])            # ranks
+    np.testing.assert_array_equal(log_g[:, 12:14], log_h[:, 12:14])    # sweeps of both passes
+    np.testing.assert_allclose(log_g[:, 6], log_h[:, 6], rtol=1e-9)     # per-split f
+    assert abs(m_g.fidelity() / m_h.fidelity() - 1) <= 1e-9
+    ref = oracle.simulate(c, chi, w.cutoff, w.q_max, 0, w.k_max)
+    assert fidelity_overlap(ref, as_oracle(m_g)) >= 1 - 1e-6
+    assert abs(m_g.fidelity() / np.exp(ref.logF) - 1) <= 1e-5
+
+
+def test_switch_rejects_other_values():
+    P = lib()
+    import ctypes
+    assert P._lib.ctebd_set_sweep_graphs(ctypes.c_int(2)) != 0
