@@ -511,15 +511,29 @@ extern "C" int ctebd_set_tensor_cores(int mode) {
   return CTEBD_OK;
 }
 
-static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind) {
+static double gemm_flops(const GemmProb& g) { return 8.0 * g.M * g.N * (double)g.K * g.batch; }
+
+static double gemm_bytes(const GemmProb& g, size_t esz) {
+  return ((double)g.M * g.K * (g.sA ? g.batch : 1) + (double)g.K * g.N * (g.sB ? g.batch : 1) +
+          (double)g.M * g.N * g.batch) * esz;
+}
+
+// the tensor-core kernel copies operand chunks with 16-byte cp.async when
+// every granule it copies starts on a 16-byte boundary
+static int tc_async_ok(const GemmProb& g) {
+  const bool a_al = ((uintptr_t)g.A & 15) == 0 && g.lda % 2 == 0 && (g.batch == 1 || g.sA % 2 == 0);
+  const bool b_al = ((uintptr_t)g.B & 15) == 0 && g.ldb % 2 == 0 && (g.batch == 1 || g.sB % 2 == 0);
+  return a_al && b_al ? 1 : 0;
+}
+
+// one grouped launch of probs on the tensor cores (tc) or the SIMT kernel
+static int launch_gemm_group(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind, bool tc) {
   if (probs.empty()) return CTEBD_OK;
   double fl = 0, by = 0;
   for (const GemmProb& g : probs) {
-    fl += 8.0 * g.M * g.N * (double)g.K * g.batch;
-    by += ((double)g.M * g.K * (g.sA ? g.batch : 1) + (double)g.K * g.N * (g.sB ? g.batch : 1) +
-           (double)g.M * g.N * g.batch) * m->esz;
+    fl += gemm_flops(g);
+    by += gemm_bytes(g, m->esz);
   }
-  const bool tc = !m->fp64 && (g_tc_mode == 2 || (g_tc_mode == 1 && fl >= 2e9));
   std::vector<long long> off(probs.size() + 1, 0);
   for (size_t i = 0; i < probs.size(); i++)
     off[i + 1] = off[i] + (tc ? tc_gemm_tiles(probs[i]) : gemm_tiles(probs[i], m->fp64));
@@ -542,6 +556,27 @@ static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind)
                           : launch_gemm<float>(dp, doff, (int)probs.size(), off.back(), m->stream);
   CUDA_TRY(e);
   return CTEBD_OK;
+}
+
+// Size policy (mode 1): a group of at least 2 GFLOP goes to the tensor cores,
+// except its problems with fewer than 64 rows -- the tensor-core tile is 128
+// rows -- which run on the SIMT kernel in a second launch.
+static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind) {
+  if (probs.empty()) return CTEBD_OK;
+  if (m->fp64 || g_tc_mode == 0) return launch_gemm_group(m, probs, kind, false);
+  if (g_tc_mode == 2) {
+    std::vector<GemmProb> all(probs);
+    for (GemmProb& g : all) g.async_ok = tc_async_ok(g);
+    return launch_gemm_group(m, all, kind, true);
+  }
+  double fl = 0;
+  for (const GemmProb& g : probs) fl += gemm_flops(g);
+  if (fl < 2e9) return launch_gemm_group(m, probs, kind, false);
+  std::vector<GemmProb> tc, simt;
+  for (const GemmProb& g : probs) (g.M >= 64 ? tc : simt).push_back(g);
+  for (GemmProb& g : tc) g.async_ok = tc_async_ok(g);
+  TRY(launch_gemm_group(m, tc, kind, true));
+  return launch_gemm_group(m, simt, kind, false);
 }
 
 static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -653,6 +688,9 @@ static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<co
   }
   // U (host c128) -> device run precision, then theta' = U theta per left index
   std::vector<GemmProb> probs;
+  std::vector<ApplyUProb> small;
+  long long max_cols = 0;
+  double u_flops = 0, u_bytes = 0;
   for (size_t i = 0; i < ws.size(); i++) {
     Work& w = ws[i];
     const long long D = 1LL << w.k;
@@ -666,6 +704,16 @@ static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<co
                             : launch_convert_from_c128<float>(dU, Ud, D * D, m->stream);
     CUDA_TRY(e);
     void* dst = (src == w.bufA) ? w.bufB : w.bufA;
+    if (D <= 16) {   // small clusters: streaming transform of the (a, b) columns
+      ApplyUProb u{};
+      u.U = Ud; u.src = src; u.dst = dst; u.chiL = w.chiL; u.chiR = w.chiR; u.D = (int)D;
+      small.push_back(u);
+      max_cols = std::max(max_cols, (long long)w.chiL * w.chiR);
+      u_flops += 8.0 * D * D * w.chiL * (double)w.chiR;
+      u_bytes += 2.0 * D * w.chiL * (double)w.chiR * m->esz;
+      if (dst != w.bufA) std::swap(w.bufA, w.bufB);
+      continue;
+    }
     GemmProb p{};
     p.M = (int)D; p.N = w.chiR; p.K = (int)D; p.batch = w.chiL;
     p.A = Ud; p.lda = (int)D; p.opA = 0; p.sA = 0;
@@ -676,6 +724,13 @@ static int merge_apply(ctebd_mps* m, std::vector<Work>& ws, const std::vector<co
       // keep theta' in bufA: swap the roles of the two buffers for this work item
       std::swap(w.bufA, w.bufB);
     }
+  }
+  if (!small.empty()) {
+    const ApplyUProb* dsu;
+    TRY(m->stage.push(small.data(), small.size(), &dsu));
+    ProfScope ps(m->prof, m->stream, KK_GEMM_U, u_flops, u_bytes);
+    CUDA_TRY(m->fp64 ? launch_apply_u<double>(dsu, (int)small.size(), max_cols, m->stream)
+                     : launch_apply_u<float>(dsu, (int)small.size(), max_cols, m->stream));
   }
   TRY(run_gemms(m, probs, KK_GEMM_U));
   for (auto& w : ws) w.rdim = w.chiR;

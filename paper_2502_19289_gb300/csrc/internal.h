@@ -25,6 +25,8 @@ struct GemmProb {
   int kw_shift;
   double alpha;
   int kw_pow;   // 1: multiply by kw; otherwise by kw^2
+  int async_ok; // tensor-core path: A and B 16-byte aligned, even leading dimensions and
+                // batch strides -- operand chunks are then copied with cp.async
 };
 
 // One Hermitian eigenproblem of the batched block-Jacobi solver.  G and V are
@@ -64,6 +66,15 @@ struct SelProb {
                        // the full descending order
   const double* W_ext; // optional total weight ||M||_F^2 (sketched split): the
                        // weight outside the n directions counts as discarded
+};
+
+// theta'[a, s', b] = sum_s U[s', s] theta[a, s, b] for every (a, b) column,
+// theta row-major (chiL, D, chiR), U row-major D x D in the run precision.
+struct ApplyUProb {
+  const void* U;
+  const void* src;
+  void* dst;
+  int chiL, chiR, D;   // D <= 16
 };
 
 // Column permutation (mode 0: dst[r][c] = src[r][perm[c]], r < rows, c < cols)
@@ -155,6 +166,8 @@ cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const i
                                  cudaStream_t s);
 cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, const int* d_n, int n_probs,
                                  int max_n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_apply_u(const ApplyUProb* d_probs, int n_probs, long long max_cols, cudaStream_t s);
 template <typename R>
 cudaError_t launch_permute(const PermProb* d_probs, int n_probs, long long max_elems, cudaStream_t s);
 cudaError_t launch_select(const SelProb* d_probs, int n_probs, int chi_max, double cutoff, double band,

@@ -937,6 +937,48 @@ cudaError_t launch_gather(const GatherProb* d_probs, int n_probs, long long max_
 template cudaError_t launch_gather<float>(const GatherProb*, int, long long, cudaStream_t);
 template cudaError_t launch_gather<double>(const GatherProb*, int, long long, cudaStream_t);
 
+// The cluster unitary on small clusters (D = 2^k <= 16): a streaming
+// transform of every (a, b) column, U in shared memory, coalesced along b.
+// (As a GEMM its M = D rows would leave a 128-row tensor-core tile empty.)
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_u(const ApplyUProb* __restrict__ probs) {
+  using CT = typename C2<R>::T;
+  const ApplyUProb P = probs[blockIdx.y];
+  __shared__ CT Us[16 * 16];
+  const int D = P.D;
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) Us[i] = ((const CT*)P.U)[i];
+  __syncthreads();
+  const CT* src = (const CT*)P.src;
+  CT* dst = (CT*)P.dst;
+  const long long cols = (long long)P.chiL * P.chiR;
+  for (long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x; col < cols;
+       col += (long long)gridDim.x * blockDim.x) {
+    const long long a = col / P.chiR, b = col % P.chiR;
+    const long long base = a * D * (long long)P.chiR + b;
+    CT v[16];
+#pragma unroll
+    for (int s = 0; s < 16; s++) v[s] = s < D ? src[base + (long long)s * P.chiR] : cmk<CT>(0, 0);
+    for (int t = 0; t < D; t++) {
+      CT acc = cmk<CT>(0, 0);
+#pragma unroll
+      for (int s = 0; s < 16; s++)
+        if (s < D) cfma(acc, Us[t * D + s], v[s]);
+      dst[base + (long long)t * P.chiR] = acc;
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_apply_u(const ApplyUProb* d_probs, int n_probs, long long max_cols, cudaStream_t s) {
+  if (n_probs <= 0 || max_cols <= 0) return cudaSuccess;
+  long long gx = (max_cols + 255) / 256;
+  if (gx > 4096) gx = 4096;
+  k_apply_u<R><<<dim3((unsigned)gx, n_probs), 256, 0, s>>>(d_probs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply_u<float>(const ApplyUProb*, int, long long, cudaStream_t);
+template cudaError_t launch_apply_u<double>(const ApplyUProb*, int, long long, cudaStream_t);
+
 template <typename R>
 __global__ void k_permute(const PermProb* __restrict__ probs) {
   using CT = typename C2<R>::T;

@@ -36,7 +36,11 @@ constexpr int NTHREADS = 256;
 constexpr uint32_t LBO = 144, SBO = 8 * 144 + 16;
 constexpr int OP_BYTES = 16 * SBO;                 // 18688 B
 constexpr int STAGE_BYTES = 4 * OP_BYTES;          // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;
+// raw FP32 operand chunks in their source memory order (A: 128 x 16 or 16 x 128
+// complex; B: 16 x 64 or 64 x 16), two buffers, filled by cp.async one chunk ahead
+constexpr int RAW_A = TM * TKC, RAW_B = TKC * TNC;   // complex elements
+constexpr int RAW_BYTES = (RAW_A + RAW_B) * 8;       // 24576 B
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 2 * RAW_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 128;
 // kind::tf32, D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -45,6 +49,14 @@ constexpr uint32_t WAIT_LIMIT = 1u << 26;
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+// 16-byte asynchronous copy global -> shared; bytes < 16 are zero-filled
+__device__ __forceinline__ void cp16_zfill(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // shared-memory matrix descriptor (tcgen05), no swizzle
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
@@ -237,6 +249,109 @@ __device__ bool tile_product(int kc_total, LoadA loadA, LoadB loadB, Store store
   return !failed;
 }
 
+// tile_product with the operand loads taken off the critical path: fetch(raw,
+// kc0) issues the cp.async copies of chunk kc0 into a raw buffer one chunk
+// ahead, and convA / convB (raw buffer, row or k index, local k, global k)
+// read the element from it while the chunk is staged.  Same tensor-core
+// schedule, drains and error handling as tile_product.
+template <class Fetch, class ConvA, class ConvB, class Store>
+__device__ bool tile_product_async(int kc_total, Fetch fetch, ConvA convA, ConvB convB, Store store, int* err,
+                                   bool a_rows_fast, bool b_k_fast) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+  unsigned char* raw0 = base + 2 * STAGE_BYTES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (kc_total + TKC - 1) / TKC;
+  fetch(raw0, 0);
+  cp_commit();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    failed = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t d_tmem = tmem_base;
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+  float acc[128];
+  #pragma unroll
+  for (int i = 0; i < 128; i++) acc[i] = 0.f;
+  uint32_t phase[2] = {0u, 0u};
+  const float2* rawA = nullptr;
+  const float2* rawB = nullptr;
+  int kc0 = 0;
+  auto la = [&](int r, int k) { return convA(rawA, r, k - kc0, k); };
+  auto lb = [&](int k, int d) { return convB(rawB, k - kc0, d, k); };
+  for (int i = 0; i < nchunks; i++) {
+    const int sidx = i & 1;
+    unsigned char* st = base + sidx * STAGE_BYTES;
+    // the raw buffer of chunk i + 1 was last read while staging chunk i - 1
+    if (i + 1 < nchunks) fetch(raw0 + ((i + 1) & 1) * RAW_BYTES, (i + 1) * TKC);
+    cp_commit();
+    if (i >= 2) {   // chunk i-2 used this stage and this accumulator
+      if (!mbar_wait(&bar[sidx], phase[sidx])) failed = 1;
+      phase[sidx] ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (warp < 4 && !failed) drain_add(d_tmem + lane_off + sidx * TMEM_COLS, acc);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    cp_wait_prev();   // this thread's copies of chunk i have landed
+    __syncthreads();  // and everybody's
+    rawA = reinterpret_cast<const float2*>(raw0 + sidx * RAW_BYTES);
+    rawB = rawA + RAW_A;
+    kc0 = i * TKC;
+    stage_chunk(st, kc0, la, lb, a_rows_fast, b_k_fast);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (failed) break;
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(st), al = ah + OP_BYTES, bh = ah + 2 * OP_BYTES, bl = ah + 3 * OP_BYTES;
+      const uint32_t dt = d_tmem + sidx * TMEM_COLS;
+      #pragma unroll
+      for (int s = 0; s < 4; s++) {   // K = 8 real per instruction: two core matrices
+        const uint32_t o = 2u * LBO * s;
+        mma_tf32(dt, make_desc(al + o), make_desc(bh + o), s > 0 ? 1u : 0u);
+        mma_tf32(dt, make_desc(ah + o), make_desc(bl + o), 1u);
+        mma_tf32(dt, make_desc(ah + o), make_desc(bh + o), 1u);
+      }
+      mma_commit(&bar[sidx]);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy in flight past this point
+  if (!failed) {
+    for (int i = (nchunks >= 2 ? nchunks - 2 : 0); i < nchunks; i++) {
+      const int sidx = i & 1;
+      if (!mbar_wait(&bar[sidx], phase[sidx])) { failed = 1; break; }
+      phase[sidx] ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (warp < 4) drain_add(d_tmem + lane_off + sidx * TMEM_COLS, acc);
+    }
+  } else {
+    mbar_wait(&bar[0], phase[0]);
+    mbar_wait(&bar[1], phase[1]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (!failed && warp < 4) {
+    const int row = warp * 32 + lane;
+    #pragma unroll
+    for (int i = 0; i < 64; i++) store(row, i, make_float2(acc[2 * i], acc[2 * i + 1]));
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(d_tmem), "r"(2 * TMEM_COLS));
+  if (failed && threadIdx.x == 0) atomicExch(err, 1);
+  return !failed;
+}
+
 // ---------------------------------------------------------------------------
 // Plain product: C (M x N) = A (M x K) B (K x N), complex64 row-major;
 // M % 128 == 0, N % 64 == 0, K % 16 == 0.
@@ -300,7 +415,73 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmProb* __restrict__ pr
     const int m = m0 + r, n = n0 + d;
     if (m < P.M && n < P.N) Cm[(long long)m * P.ldc + n] = make_float2(alpha * v.x, alpha * v.y);
   };
-  tile_product(P.K, loadA, loadB, store, err, P.opA == 1, P.opB == 1);
+  if (!P.async_ok) {
+    tile_product(P.K, loadA, loadB, store, err, P.opA == 1, P.opB == 1);
+    return;
+  }
+  // raw chunk copies: each 16-byte granule is two complex elements of one
+  // contiguous source row; out-of-range elements are zero-filled
+  auto fetch = [&](unsigned char* raw, int k0) {
+    float2* ra = reinterpret_cast<float2*>(raw);
+    float2* rb = ra + RAW_A;
+    for (int g = threadIdx.x; g < RAW_A / 2; g += NTHREADS) {
+      int m, k, valid;
+      long long off;
+      float2* dst;
+      if (P.opA == 0) {   // rows m, 16 k each
+        const int o = g >> 3, c = (g & 7) * 2;
+        m = m0 + o; k = k0 + c;
+        valid = m < P.M ? min(2, P.K - k) : 0;
+        off = (long long)m * P.lda + k;
+        dst = ra + o * TKC + c;
+      } else {            // rows k, 128 m each
+        const int o = g >> 6, c = (g & 63) * 2;
+        k = k0 + o; m = m0 + c;
+        valid = k < P.K ? min(2, P.M - m) : 0;
+        off = (long long)k * P.lda + m;
+        dst = ra + o * TM + c;
+      }
+      valid = max(valid, 0);
+      cp16_zfill(dst, valid > 0 ? (const void*)(A + off) : (const void*)A, 8 * valid);
+    }
+    for (int g = threadIdx.x; g < RAW_B / 2; g += NTHREADS) {
+      int n, k, valid;
+      long long off;
+      float2* dst;
+      if (P.opB == 0) {   // rows k, 64 n each
+        const int o = g >> 5, c = (g & 31) * 2;
+        k = k0 + o; n = n0 + c;
+        valid = k < P.K ? min(2, P.N - n) : 0;
+        off = (long long)k * P.ldb + n;
+        dst = rb + o * TNC + c;
+      } else {            // rows n, 16 k each
+        const int o = g >> 3, c = (g & 7) * 2;
+        n = n0 + o; k = k0 + c;
+        valid = n < P.N ? min(2, P.K - k) : 0;
+        off = (long long)n * P.ldb + k;
+        dst = rb + o * TKC + c;
+      }
+      valid = max(valid, 0);
+      cp16_zfill(dst, valid > 0 ? (const void*)(B + off) : (const void*)B, 8 * valid);
+    }
+  };
+  auto convA = [&](const float2* ra, int r, int c, int k) -> float2 {
+    float2 v = P.opA == 0 ? ra[r * TKC + c] : ra[c * TM + r];
+    if (P.opA == 1) v.y = -v.y;
+    if (P.kw && k < P.K) {
+      const double w = P.kw[k >> P.kw_shift];
+      const float f = (float)(P.kw_pow == 1 ? w : w * w);
+      v.x *= f; v.y *= f;
+    }
+    return v;
+  };
+  auto convB = [&](const float2* rb, int c, int d, int k) -> float2 {
+    (void)k;
+    float2 v = P.opB == 0 ? rb[c * TNC + d] : rb[d * TKC + c];
+    if (P.opB == 1) v.y = -v.y;
+    return v;
+  };
+  tile_product_async(P.K, fetch, convA, convB, store, err, P.opA == 1, P.opB == 1);
 }
 
 long long tc_gemm_tiles(const GemmProb& p) {
