@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmProb* __restrict__ pr
     if (P.opA == 0) v = A[(long long)m * P.lda + c];
     else { v = A[(long long)c * P.lda + m]; v.y = -v.y; }
     if (P.kw) {
-      const double w = P.kw[c >> P.kw_shift];
-      const float f = (float)(P.kw_pow == 1 ? w : w * w);
+      const float w = (float)P.kw[c >> P.kw_shift];   // FP32 like the operands (FP64 is slow here)
+      const float f = P.kw_pow == 1 ? w : w * w;
       v.x *= f; v.y *= f;
     }
     return v;
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmProb* __restrict__ pr
     float2 v = P.opA == 0 ? ra[r * TKC + c] : ra[c * TM + r];
     if (P.opA == 1) v.y = -v.y;
     if (P.kw && k < P.K) {
-      const double w = P.kw[k >> P.kw_shift];
-      const float f = (float)(P.kw_pow == 1 ? w : w * w);
+      const float w = (float)P.kw[k >> P.kw_shift];   // FP32 like the operands (FP64 is slow here)
+      const float f = P.kw_pow == 1 ? w : w * w;
       v.x *= f; v.y *= f;
     }
     return v;
