@@ -397,6 +397,8 @@ struct ctebd_mps {
   uint64_t nstep = 0;
   float* mlp = nullptr;            // rank predictor parameters (device)
   int* tc_err = nullptr;           // tensor-core completion-wait timeout flag (device)
+  cudaStream_t side = nullptr;     // second branch of the device-side sweep graphs
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* arena = nullptr;
   size_t arena_cap = 0;
   Staging stage;
@@ -493,6 +495,9 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   if (m->h_res) cudaFreeHost(m->h_res);
   m->stage.release();
   m->prof.release();
+  if (m->side) cudaStreamDestroy(m->side);
+  if (m->fork_ev) cudaEventDestroy(m->fork_ev);
+  if (m->join_ev) cudaEventDestroy(m->join_ev);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
   delete m;
   return CTEBD_OK;
@@ -799,8 +804,30 @@ extern "C" int ctebd_set_sweep_graphs(int on) {
   return CTEBD_OK;
 }
 
-static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, int max_nb, double* d_cum, int max_sweeps) {
+// The problems are split into two halves captured on two streams: the graph
+// body holds two independent chains of round launches (joined before the
+// sweep-end kernel), so one half's latency-bound inner kernels can run while
+// the other half's apply kernels do.
+static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector<int>& nbs, double* d_cum,
+                           int max_sweeps) {
   const bool f64 = m->fp64;
+  if (!m->side) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming));
+  }
+  const int na0 = na > 1 ? (na + 1) / 2 : na, na1 = na - na0;
+  int nb0 = 2, nb1 = 2;
+  for (int i = 0; i < na; i++) (i < na0 ? nb0 : nb1) = std::max(i < na0 ? nb0 : nb1, nbs[i]);
+  auto chain = [&](EigProb* d, int n, int max_nb, cudaStream_t s) -> cudaError_t {
+    cudaError_t le = cudaSuccess;
+    for (int t = 0; t < max_nb - 1 && le == cudaSuccess; t++) {
+      le = f64 ? launch_eig_inner<double>(d, n, max_nb, t, s) : launch_eig_inner<float>(d, n, max_nb, t, s);
+      if (le == cudaSuccess)
+        le = f64 ? launch_eig_apply<double>(d, n, max_nb, t, s) : launch_eig_apply<float>(d, n, max_nb, t, s);
+    }
+    return le;
+  };
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   cudaGraphConditionalHandle h{};
@@ -820,13 +847,14 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, int max_nb, doubl
                                       cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t le = cudaSuccess;
-    for (int t = 0; t < max_nb - 1 && le == cudaSuccess; t++) {
-      le = f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
-               : launch_eig_inner<float>(dep, na, max_nb, t, m->stream);
-      if (le == cudaSuccess)
-        le = f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
-                 : launch_eig_apply<float>(dep, na, max_nb, t, m->stream);
+    if (na1 > 0) {   // fork the second half onto the side stream
+      le = cudaEventRecord(m->fork_ev, m->stream);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(m->side, m->fork_ev, 0);
+      if (le == cudaSuccess) le = chain(dep + na0, na1, nb1, m->side);
+      if (le == cudaSuccess) le = cudaEventRecord(m->join_ev, m->side);
     }
+    if (le == cudaSuccess) le = chain(dep, na0, nb0, m->stream);
+    if (le == cudaSuccess && na1 > 0) le = cudaStreamWaitEvent(m->stream, m->join_ev, 0);
     if (le == cudaSuccess) le = launch_sweep_end(dep, na, d_cum, d_cum + 3 * na, max_sweeps, h, m->stream);
     cudaGraph_t body = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(m->stream, &body);
@@ -895,7 +923,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
     CUDA_TRY(eig_prepare(f64));
-    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, max_nb, d_cum, max_sweeps);
+    std::vector<int> nbs(na);
+    for (int i = 0; i < na; i++) nbs[i] = eps[i].nb;
+    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps);
     std::vector<double> hc(n_cum, 0.0);
     if (rc == CTEBD_OK) {
       CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cum, sizeof(double) * n_cum, cudaMemcpyDeviceToHost, m->stream));
@@ -904,6 +934,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     cudaFreeAsync(d_cum, m->stream);
     cudaFreeAsync(d_off, m->stream);
     TRY(rc);
+    // launches: every sweep runs both halves' rounds (counted as for one batch)
     const double rounds = hc[3 * na] * (max_nb - 1);
     m->prof.launches[KK_EIG_INNER] += rounds;
     m->prof.launches[KK_EIG_APPLY] += rounds;
