@@ -1,0 +1,51 @@
+"""GPU: closed forms and degenerate cases.  GHZ states have a degenerate
+Schmidt spectrum (two equal values per bond); product states keep every bond
+at dimension 1; a step with no clusters leaves the state and F unchanged."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import download, lib, run_gpu, statevector_of
+
+pytestmark = pytest.mark.gpu
+TOL = {"FP64": 1e-12, "FP32": 2e-6}
+
+
+@pytest.mark.parametrize("precision_name", ["FP64", "FP32"])
+def test_ghz_closed_form(precision_name):
+    P = lib()
+    n = 12
+    c = synth.ghz_circuit(n)
+    mps, _ = run_gpu(c, 4, 0.0, 8, 0, 4, getattr(P, precision_name))
+    tol = TOL[precision_name]
+    assert list(mps.bond_dims()) == [1] + [2] * (n - 1) + [1]
+    for b in range(1, n):
+        np.testing.assert_allclose(mps.lam(b), [2 ** -0.5, 2 ** -0.5], atol=tol)
+    assert abs(mps.amplitude(np.zeros(n, np.uint8)) - 2 ** -0.5) < tol
+    assert abs(mps.amplitude(np.ones(n, np.uint8)) - 2 ** -0.5) < tol
+    one_hot = np.zeros(n, np.uint8)
+    one_hot[0] = 1
+    assert abs(mps.amplitude(one_hot)) < tol
+    assert abs(mps.fidelity() - 1.0) < tol
+
+
+@pytest.mark.parametrize("precision_name", ["FP64", "FP32"])
+def test_product_state_stays_chi_one(precision_name):
+    P = lib()
+    c = synth.product_circuit(9, seed=3)
+    mps, _ = run_gpu(c, 4, 0.0, 8, 0, 4, getattr(P, precision_name))
+    assert list(mps.bond_dims()) == [1] * 10
+    _, sites, _ = download(mps)
+    np.testing.assert_allclose(statevector_of(sites), oracle.statevector(c), atol=TOL[precision_name])
+
+
+def test_empty_step_changes_nothing():
+    P = lib()
+    c = synth.ghz_circuit(6)
+    mps, _ = run_gpu(c, 4, 0.0, 8, 0, 4, P.FP32)
+    before = statevector_of(download(mps)[1])
+    f = mps.step([], [])
+    assert len(f) == 0
+    np.testing.assert_array_equal(statevector_of(download(mps)[1]), before)
+    assert abs(mps.fidelity() - 1.0) < 1e-6
