@@ -173,7 +173,8 @@ def rank_features(gates, n_gates, cl: Cluster, chi, entropy, cfg: Config) -> np.
 
 
 def set_tensor_cores(mode: int):
-    """FP32 GEMM policy: 0 CUDA cores only, 1 above 2 GFLOP (default), 2 always."""
+    """FP32 GEMM policy: 0 CUDA cores only, 1 batches above 2 GFLOP (problems under 64 rows
+    on the CUDA cores; default), 2 always."""
     _check(_lib.ctebd_set_tensor_cores(int(mode)), "ctebd_set_tensor_cores")
 
 
