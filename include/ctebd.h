@@ -273,6 +273,13 @@ int ctebd_set_tensor_cores(int mode);
    Returns CTEBD_ERR_ARG for other values. */
 int ctebd_set_sweep_graphs(int on);
 
+/* Sweep cap of the Jacobi eigen-solves of the split (not in the paper; the
+   solver of this implementation), process-wide, 1..1000 (default 30).  A
+   solve whose problems still make significant rotations after n sweeps makes
+   step / truncate_split / split2_noalloc return CTEBD_ERR_NUMERIC (the state's
+   sites of that iteration are then undefined).  Errors: ARG. */
+int ctebd_set_max_sweeps(int n);
+
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0
    stops timing; launch counts and algorithmic flop/byte counts are always
@@ -284,6 +291,14 @@ int ctebd_set_sweep_graphs(int on);
 int ctebd_profile(ctebd_mps* mps, int mode);
 int ctebd_profile_read(ctebd_mps* mps, double* rows, int cap, int* n_kinds);
 int ctebd_kernel_name(int kind, char* buf, size_t n);
+
+/* FP32 CUDA-core throughput of the current device, measured (not in the
+   paper: the roofline denominator of this implementation's FP32 kernels):
+   repeats timed launches of an FMA loop (4 CTAs of 256 threads per SM, 8
+   independent chains per thread, 2 flops per FMA), after one warm-up launch.
+   Writes the best and mean TFLOP/s and the SM count.  Allocates a small
+   buffer.  Errors: ARG, CUDA. */
+int ctebd_measure_fma(int repeats, double* tflops_best, double* tflops_mean, int* n_sm);
 
 /* split2_noalloc: the two-site split (apply_cluster + truncate_split for a
    k = 2 cluster) for callers that cannot allocate device memory while they
@@ -305,11 +320,12 @@ int ctebd_kernel_name(int kind, char* buf, size_t n);
    2.4 MiB inside this library, which every GPU that loads the library holds
    until the process exits.  chi_l and chi_r are limited to 128 (larger
    values return CTEBD_ERR_ARG).  The first call on a device resolves the
-   array's device address (cudaGetSymbolAddress) with that device current;
-   make that first call before any stream capture.  Every call shares the
-   array and leaves the previous call's data in it; calls that overlap on the
-   GPU (other streams or threads) race on it.  The call synchronises
-   cuda_stream (NULL: the legacy default stream) before returning.
+   array's device address (cudaGetSymbolAddress) with that device current.
+   Every call copies descriptors from pageable host memory, reads results
+   back and synchronises cuda_stream (NULL: the legacy default stream) before
+   returning, so it cannot be called while that stream is being captured.
+   Every call shares the array and leaves the previous call's data in it;
+   calls that overlap on the GPU (other streams or threads) race on it.
    Errors: ARG, CUDA, NUMERIC. */
 int split2_noalloc(const void* theta, const double* lam_l, int chi_l, int chi_r, int chi_max,
                    double cutoff, void* site_l_out, void* site_r_out, double* lam_out,

@@ -191,6 +191,36 @@ def split_fidelity(M: np.ndarray, w: np.ndarray, chi_max: int, cutoff: float, fl
     return r, f, W, s
 
 
+def split_chain(theta: np.ndarray, lam_l: np.ndarray, chi_max: int, cutoff: float,
+                floor: float = 1e-13):
+    """The k-1 truncated splits of one cluster update (Sec. III.A, Fig. 2 and
+    Fig. 3), right to left, in the gauge of MPS.cluster_update: split j
+    factors diag(lambda_L) Rbar_j (chi_L 2^j x 2 r_{j+1}); the kept right
+    singular vectors give the new site, the unweighted remainder Rbar_j Y_r /
+    sqrt(kept) feeds split j-1.  theta: (chi_L, 2^k, chi_R) with the cluster
+    unitary applied and without the left weights.  The SVD is LAPACK's (numpy),
+    a library step; sizes up to a few thousand.  Returns one dict per split,
+    rightmost bond first: j (bond q0 + j), m, n, r, f (Eq. 4), W, s, lam."""
+    th = np.asarray(theta, dtype=np.complex128)
+    cl, D, cr = th.shape
+    k = int(round(np.log2(D)))
+    lam_l = np.asarray(lam_l, dtype=np.float64)
+    R, rdim, out = th.reshape(-1), cr, []
+    for j in range(k - 1, 0, -1):
+        m, n = cl << j, 2 * rdim
+        Mb = R.reshape(m, n)
+        w = np.repeat(lam_l, 1 << j)
+        _, s, Vh = np.linalg.svd(w[:, None] * Mb, full_matrices=False)
+        r = truncation_rank(s, chi_max, cutoff, floor)
+        W = float(np.sum(s * s))
+        kept = float(np.sum(s[:r] ** 2))
+        out.append({"j": j, "m": m, "n": n, "r": r, "f": kept / W if W > 0 else 1.0, "W": W,
+                    "s": s, "lam": s[:r] / np.sqrt(kept)})
+        R = (Mb @ Vh[:r].conj().T / np.sqrt(kept)).reshape(-1)
+        rdim = r
+    return out
+
+
 # ---- MPS (Vidal form, Sec. II.B-II.C, III.A) --------------------------------
 class MPS:
     """Oracle MPS: right-canonical sites B_q (chi_q, 2, chi_{q+1}) + spectra."""

@@ -84,6 +84,8 @@ def _load():
         "tc_cgemm": [P, P, P, I, I, I, P],
         "ctebd_set_tensor_cores": [I],
         "ctebd_set_sweep_graphs": [I],
+        "ctebd_set_max_sweeps": [I],
+        "ctebd_measure_fma": [I, C.POINTER(D), C.POINTER(D), C.POINTER(I)],
         "mlp_forward": [P, P, I, P, P],
         "mlp_loss_grad": [P, P, P, I, P, P, P],
         "mlp_adam": [P, P, P, P, I, C.c_float, I, P],
@@ -182,6 +184,20 @@ def set_sweep_graphs(on: bool):
     """Run each eigen-solve's sweep loop on the device as one CUDA graph (default)
     or launch every round from the host; process-wide (ctebd_set_sweep_graphs)."""
     _check(_lib.ctebd_set_sweep_graphs(int(bool(on))), "ctebd_set_sweep_graphs")
+
+
+def set_max_sweeps(n: int):
+    """Sweep cap of the Jacobi eigen-solves (default 30); a solve still rotating at
+    the cap makes the split fail with CTEBD_ERR_NUMERIC; process-wide."""
+    _check(_lib.ctebd_set_max_sweeps(int(n)), "ctebd_set_max_sweeps")
+
+
+def measure_fma(repeats: int = 5):
+    """Measured FP32 CUDA-core throughput: (best TFLOP/s, mean TFLOP/s, SM count)."""
+    best, mean, sms = C.c_double(0), C.c_double(0), C.c_int(0)
+    _check(_lib.ctebd_measure_fma(int(repeats), C.byref(best), C.byref(mean), C.byref(sms)),
+           "ctebd_measure_fma")
+    return best.value, mean.value, sms.value
 
 
 def tc_cgemm(A_ptr, B_ptr, C_ptr, M, K, N, stream=None):

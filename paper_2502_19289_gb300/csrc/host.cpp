@@ -797,6 +797,17 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // off (ctebd_set_sweep_graphs; process-wide).
 // ---------------------------------------------------------------------------
 static int g_sweep_graphs = 1;
+static int g_max_sweeps = 30;
+
+namespace ctebd {
+int max_jacobi_sweeps() { return g_max_sweeps; }
+}  // namespace ctebd
+
+extern "C" int ctebd_set_max_sweeps(int n) {
+  if (n < 1 || n > 1000) return fail(CTEBD_ERR_ARG, "ctebd_set_max_sweeps: 1..1000");
+  g_max_sweeps = n;
+  return CTEBD_OK;
+}
 
 extern "C" int ctebd_set_sweep_graphs(int on) {
   if (on < 0 || on > 1) return fail(CTEBD_ERR_ARG, "ctebd_set_sweep_graphs: 0 or 1");
@@ -914,7 +925,12 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
                  : launch_eig_init<float>(dep, na, max_npad, m->stream));
     CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
   }
-  const int max_sweeps = 30;
+  const int max_sweeps = g_max_sweeps;
+  auto not_converged = [&](int count) {
+    return fail(CTEBD_ERR_NUMERIC, "Jacobi eigen-solve: " + std::to_string(count) + " of " +
+                                       std::to_string(na) + " problems still rotating after " +
+                                       std::to_string(max_sweeps) + " sweeps");
+  };
   if (g_sweep_graphs && !m->prof.on) {
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
     double* d_cum = nullptr;
@@ -927,8 +943,10 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     for (int i = 0; i < na; i++) nbs[i] = eps[i].nb;
     const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps);
     std::vector<double> hc(n_cum, 0.0);
+    std::vector<EigProb> fin(na);   // descriptors after the loop: active = still rotating
     if (rc == CTEBD_OK) {
       CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cum, sizeof(double) * n_cum, cudaMemcpyDeviceToHost, m->stream));
+      CUDA_TRY(cudaMemcpyAsync(fin.data(), dep, sizeof(EigProb) * na, cudaMemcpyDeviceToHost, m->stream));
       CUDA_TRY(cudaStreamSynchronize(m->stream));
     }
     cudaFreeAsync(d_cum, m->stream);
@@ -944,6 +962,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       m->prof.flops[KK_EIG_APPLY] += hc[3 * i + 1];
       sweeps[sel[i]] += (int)hc[3 * i + 2];
     }
+    int left = 0;
+    for (int i = 0; i < na; i++) left += fin[i].active ? 1 : 0;
+    if (left) return not_converged(left);
     return CTEBD_OK;
   }
   std::vector<double> hoff(3 * na);
@@ -992,6 +1013,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     TRY(m->stage.push(eps.data(), eps.size(), &dep));
   }
   CUDA_TRY(cudaFreeAsync(d_off, m->stream));
+  int left = 0;
+  for (int i = 0; i < na; i++) left += eps[i].active ? 1 : 0;
+  if (left) return not_converged(left);
   return CTEBD_OK;
 }
 
@@ -1056,6 +1080,7 @@ static int level_project_select(ctebd_mps* m, std::vector<Work>& ws, const Level
     sp[i].rho = w.rho; sp[i].n = L.ne[a]; sp[i].perm = w.perm;
     sp[i].lam_out = m->lam[w.q0 + L.shift[a]]; sp[i].res = w.res;
     sp[i].W_ext = L.sk[a] ? w.res + 8 : nullptr;
+    sp[i].rank_cap = L.mm[a];
     if (L.ne[a] > 4096) return fail(CTEBD_ERR_ARG, "split wider than 4096");
   }
   const SelProb* dsp;
@@ -1810,6 +1835,42 @@ extern "C" int ctebd_profile_read(ctebd_mps* m, double* rows, int cap, int* n_ki
     rows[5 * k + 3] = m->prof.bytes[k];
     rows[5 * k + 4] = m->prof.tc[k];
   }
+  return CTEBD_OK;
+}
+
+extern "C" int ctebd_measure_fma(int repeats, double* tflops_best, double* tflops_mean, int* n_sm) {
+  if (repeats < 1 || !tflops_best || !tflops_mean || !n_sm) return fail(CTEBD_ERR_ARG, "ctebd_measure_fma: bad args");
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  float* out = nullptr;
+  int rc = CTEBD_OK;
+  const int blocks = 4 * sms, iters = 1 << 19;
+  double best = 0, sum = 0;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess || cudaMalloc(&out, sizeof(float) * blocks * 256) != cudaSuccess) {
+    rc = fail(CTEBD_ERR_CUDA, "ctebd_measure_fma: setup");
+  }
+  for (int r = -1; r < repeats && rc == CTEBD_OK; r++) {   // r = -1: warm-up
+    cudaEventRecord(a, s);
+    if (launch_fma_peak(out, blocks, iters, s) != cudaSuccess) { rc = fail(CTEBD_ERR_CUDA, "fma probe launch"); break; }
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) { rc = fail(CTEBD_ERR_CUDA, "fma probe"); break; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    const double tf = 2.0 * 8.0 * iters * (double)blocks * 256 / (ms * 1e-3) / 1e12;
+    if (r >= 0) { best = std::max(best, tf); sum += tf; }
+  }
+  if (out) cudaFree(out);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (s) cudaStreamDestroy(s);
+  if (rc != CTEBD_OK) return rc;
+  *tflops_best = best;
+  *tflops_mean = sum / repeats;
+  *n_sm = sms;
   return CTEBD_OK;
 }
 

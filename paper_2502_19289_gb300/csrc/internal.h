@@ -66,6 +66,8 @@ struct SelProb {
                        // the full descending order
   const double* W_ext; // optional total weight ||M||_F^2 (sketched split): the
                        // weight outside the n directions counts as discarded
+  int rank_cap;        // > 0: the rank of the split matrix is at most rank_cap (its
+                       // row count): no more directions than that are kept
 };
 
 // theta'[a, s', b] = sum_s U[s', s] theta[a, s, b] for every (a, b) column,
@@ -204,5 +206,11 @@ cudaError_t launch_tc_gemm(const GemmProb* d_probs, const long long* d_tile_off,
 
 // message returned by ctebd_last_error() in the calling thread
 void set_last_error(const std::string& msg);
+
+// FP32 FMA throughput probe: blocks x 256 threads x 8 chains x iters FMAs
+cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s);
+
+// sweep cap of the Jacobi eigen-solves (ctebd_set_max_sweeps; default 30)
+int max_jacobi_sweeps();
 
 }  // namespace ctebd

@@ -799,7 +799,8 @@ cudaError_t launch_rho_normalize(double* const* d_rho, double* const* d_vn, cons
 // ---------------------------------------------------------------------------
 // Truncation (Sec. II.B): sort the weights descending, keep the smallest r
 // whose discarded weight is <= cutoff * total, drop numerical zeros
-// (rho <= floor2 * rho_max), cap at chi_max; f = kept / total (Eq. 4); the
+// (rho <= floor2 * rho_max), keep no more than the matrix's rank bound
+// (rank_cap) and chi_max; f = kept / total (Eq. 4); the
 // kept spectrum is renormalised to unit weight.
 // ---------------------------------------------------------------------------
 constexpr int SEL_MAX = 4096;
@@ -856,6 +857,7 @@ __global__ void __launch_bounds__(1024) k_select(const SelProb* __restrict__ pro
     int nz = 0;
     for (int i = 0; i < n; i++) nz += key[i] > floor2 * key[0] ? 1 : 0;
     if (nz < r) r = nz;
+    if (P.rank_cap > 0 && r > P.rank_cap) r = P.rank_cap;   // rank(M) <= its row count
     if (r < 1) r = 1;
     P.res[4] = r;
     if (r > chi_max) r = chi_max;
@@ -1117,5 +1119,28 @@ template cudaError_t launch_convert_from_c128<float>(const double*, void*, long 
 template cudaError_t launch_convert_from_c128<double>(const double*, void*, long long, cudaStream_t);
 template cudaError_t launch_convert_to_c128<float>(const void*, double*, long long, cudaStream_t);
 template cudaError_t launch_convert_to_c128<double>(const void*, double*, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput probe (the CUDA-core roofline of the FP32 kernels):
+// every thread runs 8 independent FMA chains; 2 flops per FMA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ out, int iters, float x, float y) {
+  float a[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) a[i] = x + 1e-7f * (float)threadIdx.x + (float)i;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) a[i] = fmaf(a[i], y, x);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; i++) sum += a[i];
+  if (sum == 1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;   // keeps the chains live
+}
+
+cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s) {
+  k_fma_peak<<<blocks, 256, 0, s>>>(out, iters, 1e-3f, 0.999f);
+  return cudaGetLastError();
+}
 
 }  // namespace ctebd

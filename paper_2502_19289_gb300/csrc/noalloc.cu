@@ -114,19 +114,23 @@ static int na_gemm(NaDesc& d, const GemmProb& p) {
 // stopping rule as the handle path.
 static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor,
                   double rel_skip) {
-  double* cnt = (double*)(S + NA_OFF_CNT);   // [0] significant, [1] all, [2] trace
+  // [0] significant rotations, [1] all rotations, [2] applied flops (the
+  // kernels' third counter, unused without pair flags), [3] trace of G
+  double* cnt = (double*)(S + NA_OFF_CNT);
   EigProb e{};
   e.G = S + NA_OFF_G; e.V = acc; e.J = S + NA_OFF_J;
   e.npad = npad; e.nb = npad / NA_JB; e.active = 1;
-  e.off = cnt; e.scale = cnt + 2; e.floor_factor = floor_factor;
+  e.off = cnt; e.scale = cnt + 3; e.floor_factor = floor_factor;
   e.rel_skip = rel_skip;   // no pair flags: every tile is updated
   const EigProb* de;
   const size_t mark = d.off;
   if (int rc = d.put(&e, 1, &de)) return rc;
   NA_CUDA(launch_eig_init<float>(de, 1, npad, d.s));
   NA_CUDA(launch_eig_trace<float>(de, 1, d.s));
-  for (int sweep = 0; sweep < 30; sweep++) {
-    NA_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(double), d.s));
+  const int max_sweeps = max_jacobi_sweeps();
+  bool converged = false;
+  for (int sweep = 0; sweep < max_sweeps && !converged; sweep++) {
+    NA_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(double), d.s));
     for (int t = 0; t < e.nb - 1; t++) {
       NA_CUDA(launch_eig_inner<float>(de, 1, e.nb, t, d.s));
       NA_CUDA(launch_eig_apply<float>(de, 1, e.nb, t, d.s));
@@ -134,9 +138,12 @@ static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor
     double h[2] = {0, 0};
     NA_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, d.s));
     NA_CUDA(cudaStreamSynchronize(d.s));
-    if (h[0] == 0.0) break;
+    converged = h[0] == 0.0;
   }
   d.off = mark;
+  if (!converged)
+    return na_fail(CTEBD_ERR_NUMERIC, "split2_noalloc: Jacobi eigen-solve still rotating after " +
+                                          std::to_string(max_sweeps) + " sweeps");
   return CTEBD_OK;
 }
 
@@ -211,6 +218,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     SelProb sp{};
     sp.rho = (double*)(S + NA_OFF_RHO); sp.n = n; sp.perm = (int*)(S + NA_OFF_PERM);
     sp.lam_out = lam_out; sp.res = (double*)(S + NA_OFF_RES);
+    sp.rank_cap = std::min(m, n);   // lam_out and site_l_out hold at most min(chi_max, m, n)
     const SelProb* dsp;
     if (int rc = d.put(&sp, 1, &dsp)) return rc;
     NA_CUDA(launch_select(dsp, 1, chi_max, cutoff, 0.0, 0.0, 1e-12, s));
@@ -242,7 +250,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
   }
   const int r = (int)res[0];
   const double kept = res[3];
-  if (!(kept > 0) || r < 1 || r > n || r > chi_max)
+  if (!(kept > 0) || r < 1 || r > n || r > m || r > chi_max)
     return na_fail(CTEBD_ERR_NUMERIC, "split2_noalloc: zero weight or rank out of range");
   GatherProb g[2] = {};
   g[0].src = V; g[0].dst = site_r_out; g[0].perm = (int*)(S + NA_OFF_PERM);

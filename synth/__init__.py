@@ -215,6 +215,36 @@ def ghz_circuit(n: int) -> Circuit:
     return b.build()
 
 
+def bell_pairs_circuit(n: int, pairs) -> Circuit:
+    """Bell pairs (|00> + |11>)/sqrt2 between the listed qubit pairs, every
+    other qubit left in |0>, with nearest-neighbour gates only: each pair is
+    made on two adjacent qubits (H, CNOT), then adjacent SWAPs (a bubble sort)
+    carry every qubit to its listed position."""
+    pairs = [tuple(p) for p in pairs]
+    used = [q for p in pairs for q in p]
+    if len(set(used)) != len(used) or any(q < 0 or q >= n for q in used):
+        raise ValueError("pairs must be disjoint qubits in range")
+    free = [q for q in range(n) if q not in used]
+    target = []                       # final position of the qubit at each start position
+    for a, b in pairs:
+        target += [a, b]
+    target += free
+    b = _Builder(n)
+    for i in range(len(pairs)):
+        b.g1(H, 2 * i)
+        b.g2(CNOT, 2 * i, 2 * i + 1)
+    t = list(target)
+    changed = True
+    while changed:
+        changed = False
+        for i in range(n - 1):
+            if t[i] > t[i + 1]:
+                b.g2(SWAP, i, i + 1)
+                t[i], t[i + 1] = t[i + 1], t[i]
+                changed = True
+    return b.build()
+
+
 def product_circuit(n: int, seed: int = 0) -> Circuit:
     rng = np.random.default_rng(seed)
     b = _Builder(n)

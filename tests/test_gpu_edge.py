@@ -49,3 +49,30 @@ def test_empty_step_changes_nothing():
     assert len(f) == 0
     np.testing.assert_array_equal(statevector_of(download(mps)[1]), before)
     assert abs(mps.fidelity() - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_sweep_cap_reports_numeric_error(graphs):
+    """A Jacobi eigen-solve still rotating at the sweep cap is an error
+    (CTEBD_ERR_NUMERIC), never a silently unconverged split.  One sweep cannot
+    diagonalise a random 128-wide split; the default cap solves it."""
+    P = lib()
+    chis, sites, lams = synth.random_right_canonical(12, 64, seed=77)
+    U = np.linalg.qr(np.random.default_rng(77).standard_normal((4, 4)))[0].astype(np.complex128)
+    cfg = P.make_config(12, 64, 1e-8, 2 + 12 + 2, 0, 2, P.FP32)
+    try:
+        P.set_sweep_graphs(graphs)
+        P.set_max_sweeps(1)
+        mps = P.MPS(cfg)
+        mps.load(chis, sites, lams)
+        with pytest.raises(P.CtebdError, match="still rotating after 1 sweeps"):
+            mps.step([P.Cluster(5, 2, 0, 0)], [U])
+    finally:
+        P.set_max_sweeps(30)
+        P.set_sweep_graphs(True)
+    mps = P.MPS(cfg)
+    mps.load(chis, sites, lams)
+    f = mps.step([P.Cluster(5, 2, 0, 0)], [U])
+    assert 0.0 < f[0] <= 1.0
+    with pytest.raises(P.CtebdError):
+        P.set_max_sweeps(0)

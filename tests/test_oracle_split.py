@@ -84,3 +84,55 @@ def test_flat_spectrum_large_rank_budget():
     r, f, W, sv = oracle.split_fidelity(M, np.ones(n), n // 2, 1e-14)
     assert r == n // 2
     assert abs(f - np.sum(s[: n // 2] ** 2)) < 1e-12
+
+
+def _cluster_theta(sites, q0, k, U):
+    t = sites[q0].astype(np.complex128)
+    for j in range(1, k):
+        t = np.tensordot(t, sites[q0 + j].astype(np.complex128), axes=([t.ndim - 1], [0]))
+    cl, cr = t.shape[0], t.shape[-1]
+    return np.einsum("st,atb->asb", U, t.reshape(cl, 1 << k, cr))
+
+
+def test_split_chain_matches_oracle_cluster_update():
+    """The chained splits of a k = 3 and a k = 4 cluster against the C oracle's
+    cluster update (its own Jacobi SVD, merge and remainder): same ranks at
+    every bond, fidelities and spectra to rounding, truncated and untruncated."""
+    rng = np.random.default_rng(21)
+    for seed, k, chi, chi_max, eta in [(31, 3, 8, 64, 0.0), (32, 3, 8, 5, 1e-3),
+                                       (33, 4, 4, 6, 1e-2), (34, 4, 8, 64, 1e-4)]:
+        chis, sites, lams = synth.random_right_canonical(8, chi, seed)
+        U = _haar(1 << k, rng)
+        q0 = 2
+        th = _cluster_theta(sites, q0, k, U)
+        chain = oracle.split_chain(th, lams[q0], chi_max, eta)
+        m = oracle.MPS.from_arrays(sites, lams)
+        f_c, r_c = m.cluster_update(q0, k, U, chi_max, eta)
+        assert [c["j"] for c in chain] == list(range(k - 1, 0, -1))
+        assert [c["r"] for c in chain] == [int(x) for x in r_c], (seed, r_c)
+        np.testing.assert_allclose([c["f"] for c in chain], f_c, rtol=1e-11)
+        for c in chain:
+            np.testing.assert_allclose(c["lam"], m.lam(q0 + c["j"]), rtol=1e-9, atol=1e-13)
+
+
+def test_degenerate_cut_closed_form():
+    """A stabilizer state has flat Schmidt spectra (Gottesman-Knill): six Bell
+    pairs straddle the bond between qubits 6 and 7, and a Bell pair made on
+    qubits 6, 7 by the cluster's H, CNOT gives a flat spectrum of 2^7 values.
+    chi_max = 100 cuts inside that degenerate group: whichever 100 directions
+    are kept, f = 100/128 (Eq. 4) and every kept lambda is 1/10."""
+    c = synth.bell_pairs_circuit(14, [(j, j + 8) for j in range(6)])
+    m = oracle.simulate(c, 64, 0.0, 16, 0, 4)
+    assert list(m.chi()[6:9]) == [64, 64, 64]
+    Hd = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    CN = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]])
+    U = CN @ np.kron(Hd, np.eye(2))
+    f, r = m.cluster_update(6, 2, U, 100, 0.0)
+    assert int(r[0]) == 100 and m.chi()[7] == 100
+    assert abs(f[0] - 100 / 128) < 1e-12
+    np.testing.assert_allclose(m.lam(7), np.full(100, 0.1), atol=1e-12)
+    # without the cut the same update is exact and the bond holds all 128 values
+    m2 = oracle.simulate(c, 64, 0.0, 16, 0, 4)
+    f2, r2 = m2.cluster_update(6, 2, U, 128, 0.0)
+    assert int(r2[0]) == 128 and abs(f2[0] - 1.0) < 1e-12
+    np.testing.assert_allclose(m2.lam(7), np.full(128, 2 ** -3.5), atol=1e-12)
