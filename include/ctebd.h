@@ -147,6 +147,30 @@ int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c
 int cluster_rank_bounds(const ctebd_gate* gates, int n_gates, const ctebd_cluster* c,
                         const int* chi, int* out);
 
+/* Sec. III.B, Eq. 9: bond dimensions of the virtual MPS of the circuit section
+   of layers (layer_start, layer_start + l_max] (l_max <= 0: every later
+   layer): out[b] = min(2^E(b) chi[b], chi_max, 2^min(b, N - b)) for b = 0..N,
+   where E(b) counts the multi-qubit gates of the section spanning bond b
+   (a gate on qubits q..q+w-1 spans bonds q+1..q+w-1) and chi holds the current
+   bond dimensions (N+1).  entangling (N+1, may be NULL) receives E(b).  Gates
+   must carry layers (assign_layers).  Pure host function.  Errors: ARG. */
+int virtual_mps_bonds(const ctebd_gate* gates, int n_gates, int n_qubits, int layer_start, int l_max,
+                      const int* chi, int chi_max, int* out, int* entangling);
+
+/* Sec. III.B, Eqs. 10-11: grouping of the N sites of a virtual MPS (chi_v,
+   N+1 bond dimensions, e.g. from virtual_mps_bonds) by recursive
+   bipartitioning.  A segment of sites lo..hi-1 is a group when
+   (hi - lo) + log2 chi_v[lo] + log2 chi_v[hi] <= q_max (the chain's end bonds
+   count as 1, which is Eq. 10 for the end segments); otherwise it is cut at
+   the bond of smallest chi_v among the cuts that leave neither part larger
+   than (1 + imbalance) * ceil((hi - lo) / 2) sites (ties: the most central),
+   and both parts recur.  Writes the first site of every group in ascending
+   order (up to cap) and *n_groups.  Pure host function.
+   Errors: ARG (bad arguments, cap too small), STATE (a single site with its
+   bonds exceeds q_max). */
+int adaptive_grouping(const int* chi_v, int n_qubits, int q_max, double imbalance, int* group_start,
+                      int cap, int* n_groups);
+
 /* One-qubit gate on a qubit outside every cluster (applied to its site's
    physical index; the paper is silent on such qubits).  u: 2x2 complex128
    row-major host array.  Errors: ARG, CUDA. */

@@ -16,6 +16,7 @@ state vector, the Fig. 7 caption, stabilizer entropies, finite differences).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -314,6 +315,60 @@ class MPS:
 def simulate(circ, chi_max, cutoff, q_max, l_max=0, k_max=0, floor=1e-13) -> MPS:
     """Cluster-TEBD from |0...0> over the whole circuit (Sec. III.A)."""
     return MPS(circ.n_qubits).run(circ, chi_max, cutoff, q_max, l_max, k_max, floor)
+
+
+# ---- Sec. III.B: virtual MPS (Eq. 9) and adaptive grouping (Eqs. 10-11) -----
+def virtual_bonds(n: int, gates: np.ndarray, layer: np.ndarray, layer_start: int, l_max: int,
+                  chi, chi_max: int):
+    """Eq. 9: for every bond b = 0..n (b qubits on its left), E(b) = number of
+    multi-qubit gates with layer_start < layer <= layer_start + l_max (all later
+    layers for l_max <= 0) that span bond b, and the virtual bond dimension
+    min(2^E(b) chi_b, chi_max, 2^min(b, n - b)).  Plain loops."""
+    E = [0] * (n + 1)
+    for g, L in zip(np.asarray(gates).reshape(-1, 5), layer):
+        nq = int(g[0])
+        if nq < 2 or L <= layer_start or (l_max > 0 and L > layer_start + l_max):
+            continue
+        qs = [int(q) for q in g[1:1 + nq]]
+        for b in range(min(qs) + 1, max(qs) + 1):
+            E[b] += 1
+    out = []
+    for b in range(n + 1):
+        out.append(min(2 ** E[b] * int(chi[b]), chi_max, 2 ** min(b, n - b)))
+    return np.array(out, dtype=np.int64), np.array(E, dtype=np.int64)
+
+
+def grouping(chi_v, q_max: int, imbalance: float = 1.0 / 3.0):
+    """Eqs. 10-11: recursive bipartitioning of the virtual MPS.  A segment of
+    sites [lo, hi) is accepted when its qubit count plus log2 of its two
+    boundary bonds (1 at the chain ends) is at most q_max; otherwise it is cut
+    at its bond of smallest virtual dimension, among cuts leaving each part at
+    most (1 + imbalance) * ceil(size / 2) sites (ties: the most central, then
+    the leftmost), and both parts are examined in turn.  Returns the group
+    start sites in ascending order; raises ValueError when a single site does
+    not fit."""
+    chi_v = [int(x) for x in chi_v]
+    n = len(chi_v) - 1
+
+    def bond(b):
+        return 1 if b in (0, n) else chi_v[b]
+
+    def fits(lo, hi):
+        # (hi - lo) + log2 chi_lo + log2 chi_hi <= q_max, in integers
+        return (1 << (hi - lo)) * bond(lo) * bond(hi) <= (1 << q_max) if q_max >= 0 else False
+
+    def split(lo, hi):
+        if fits(lo, hi):
+            return [lo]
+        size = hi - lo
+        if size == 1:
+            raise ValueError(f"site {lo} does not fit")
+        limit = math.floor((1.0 + imbalance) * ((size + 1) // 2) + 1e-9)
+        cands = [k for k in range(lo + 1, hi) if k - lo <= limit and hi - k <= limit]
+        k = min(cands, key=lambda c: (bond(c), abs(2 * c - (lo + hi)), c))
+        return split(lo, k) + split(k, hi)
+
+    return split(0, n)
 
 
 # ---- Gottesman-Knill pin ----------------------------------------------------

@@ -85,6 +85,8 @@ def _load():
         "ctebd_set_tensor_cores": [I],
         "ctebd_set_sweep_graphs": [I],
         "ctebd_set_max_sweeps": [I],
+        "virtual_mps_bonds": [C.POINTER(Gate), I, I, I, I, C.POINTER(I), I, C.POINTER(I), C.POINTER(I)],
+        "adaptive_grouping": [C.POINTER(I), I, I, D, C.POINTER(I), I, C.POINTER(I)],
         "ctebd_measure_fma": [I, C.POINTER(D), C.POINTER(D), C.POINTER(I)],
         "mlp_forward": [P, P, I, P, P],
         "mlp_loss_grad": [P, P, P, I, P, P, P],
@@ -162,6 +164,27 @@ def cluster_rank_bounds(gates, n_gates, cl: Cluster, chi) -> np.ndarray:
     _check(_lib.cluster_rank_bounds(gates, n_gates, C.byref(cl), _ip(chi), _ip(out)),
            "cluster_rank_bounds")
     return out[: cl.k - 1]
+
+
+def virtual_mps_bonds(gates, n_gates, n_qubits, layer_start, l_max, chi, chi_max):
+    """Eq. 9 virtual-MPS bond dimensions (N+1) and the entangling-gate counts E(b)."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    out = np.zeros(n_qubits + 1, dtype=np.int32)
+    ent = np.zeros(n_qubits + 1, dtype=np.int32)
+    _check(_lib.virtual_mps_bonds(gates, n_gates, n_qubits, int(layer_start), int(l_max), _ip(chi),
+                                  int(chi_max), _ip(out), _ip(ent)), "virtual_mps_bonds")
+    return out, ent
+
+
+def adaptive_grouping(chi_v, q_max, imbalance=1.0 / 3.0):
+    """Eqs. 10-11 recursive min-cut grouping: the first site of every group."""
+    chi_v = np.ascontiguousarray(chi_v, dtype=np.int32)
+    n = len(chi_v) - 1
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    ng = C.c_int(0)
+    _check(_lib.adaptive_grouping(_ip(chi_v), n, int(q_max), float(imbalance), _ip(out), len(out),
+                                  C.byref(ng)), "adaptive_grouping")
+    return out[: ng.value]
 
 
 def rank_features(gates, n_gates, cl: Cluster, chi, entropy, cfg: Config) -> np.ndarray:

@@ -292,6 +292,7 @@ struct Work {
   void* V = nullptr;
   void* W = nullptr;     // refinement accumulator
   void* J = nullptr;
+  void* T = nullptr;     // scratch of the tensor-core Jacobi round update (FP32)
   size_t eigElems = 0, jElems = 0;
   double* rho = nullptr;   // nmax weights, then nmax squared column norms of V
   int* perm = nullptr;
@@ -516,6 +517,14 @@ extern "C" int ctebd_set_tensor_cores(int mode) {
   return CTEBD_OK;
 }
 
+// the device flag that a tensor-core kernel sets when a bounded wait expires
+static int ensure_tc_err(ctebd_mps* m) {
+  if (m->tc_err) return CTEBD_OK;
+  CUDA_TRY(cudaMalloc(&m->tc_err, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
+  return CTEBD_OK;
+}
+
 static double gemm_flops(const GemmProb& g) { return 8.0 * g.M * g.N * (double)g.K * g.batch; }
 
 static double gemm_bytes(const GemmProb& g, size_t esz) {
@@ -547,10 +556,7 @@ static int launch_gemm_group(ctebd_mps* m, const std::vector<GemmProb>& probs, i
   TRY(m->stage.push(probs.data(), probs.size(), &dp));
   TRY(m->stage.push(off.data(), off.size(), &doff));
   if (tc) {
-    if (!m->tc_err) {
-      CUDA_TRY(cudaMalloc(&m->tc_err, sizeof(int)));
-      CUDA_TRY(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
-    }
+    TRY(ensure_tc_err(m));
     ProfScope ps(m->prof, m->stream, kind, fl, by);
     m->prof.tc[kind] += 1;
     CUDA_TRY(launch_tc_gemm(dp, doff, (int)probs.size(), off.back(), m->tc_err, m->stream));
@@ -611,6 +617,7 @@ static std::vector<std::pair<void**, size_t>> work_buffers(const ctebd_mps* m, W
       {&w.bufA, w.bufElems * m->esz}, {&w.bufB, w.bufElems * m->esz}, {&w.G, w.eigElems * m->esz},
       {&w.V, w.eigElems * m->esz},    {&w.W, w.eigElems * m->esz},    {&w.J, w.jElems * m->esz},
       {(void**)&w.rho, w.nmax * 16},   {(void**)&w.perm, w.nmax * 4},  {(void**)&w.res, 256}};
+  if (!m->fp64) b.push_back({&w.T, w.eigElems * m->esz});
   if (!m->fp64 && m->cfg.sketch_oversample > 0) {
     b.push_back({&w.Ys, w.bufElems / 2 * m->esz});
     b.push_back({&w.Qs, w.bufElems / 2 * m->esz});
@@ -820,7 +827,7 @@ extern "C" int ctebd_set_sweep_graphs(int on) {
 // sweep-end kernel), so one half's latency-bound inner kernels can run while
 // the other half's apply kernels do.
 static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector<int>& nbs, double* d_cum,
-                           int max_sweeps) {
+                           int max_sweeps, bool tc_apply) {
   const bool f64 = m->fp64;
   if (!m->side) {
     CUDA_TRY(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
@@ -830,12 +837,14 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector
   const int na0 = na > 1 ? (na + 1) / 2 : na, na1 = na - na0;
   int nb0 = 2, nb1 = 2;
   for (int i = 0; i < na; i++) (i < na0 ? nb0 : nb1) = std::max(i < na0 ? nb0 : nb1, nbs[i]);
+  const int JB = eig_block(f64);
   auto chain = [&](EigProb* d, int n, int max_nb, cudaStream_t s) -> cudaError_t {
     cudaError_t le = cudaSuccess;
     for (int t = 0; t < max_nb - 1 && le == cudaSuccess; t++) {
       le = f64 ? launch_eig_inner<double>(d, n, max_nb, t, s) : launch_eig_inner<float>(d, n, max_nb, t, s);
-      if (le == cudaSuccess)
-        le = f64 ? launch_eig_apply<double>(d, n, max_nb, t, s) : launch_eig_apply<float>(d, n, max_nb, t, s);
+      if (le != cudaSuccess) break;
+      if (tc_apply) le = launch_eig_apply_tc(d, n, max_nb, max_nb * JB, t, m->tc_err, s);
+      else le = f64 ? launch_eig_apply<double>(d, n, max_nb, t, s) : launch_eig_apply<float>(d, n, max_nb, t, s);
     }
     return le;
   };
@@ -896,6 +905,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     max_nb = std::max(max_nb, L.nbv[sel[i]]);
   }
   const int maxh = std::max(1, max_nb / 2);
+  // FP32 round updates on the tensor cores: policy of ctebd_set_tensor_cores
+  // (1: eigenproblems of at least 256 columns; 2: always; 0: never)
+  const bool tc_apply = !f64 && (g_tc_mode == 2 || (g_tc_mode == 1 && max_npad >= 256));
   // per problem: 3 counters (zeroed every sweep), the trace, then maxh pair flags
   double* d_off = nullptr;
   const size_t n_dbl = 4 * (size_t)na + ((size_t)na * maxh + 1) / 2;
@@ -911,12 +923,15 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     eps[i].floor_factor = floor_factor;
     eps[i].jflag = d_flag + (size_t)i * maxh;
     eps[i].rel_skip = rel_skip;
+    eps[i].T = w.T;
+    if (tc_apply && !w.T) return fail(CTEBD_ERR_STATE, "internal: no round-update scratch");
     if (use_cut) {   // columns sorted by the previous pass: [lo, hi) around the cut
       eps[i].move_rel = 1e-13;
       eps[i].cut_lo = (int)m->h_res[16 * a + 6];
       eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
     }
   }
+  if (tc_apply) TRY(ensure_tc_err(m));
   const EigProb* dep;
   TRY(m->stage.push(eps.data(), eps.size(), &dep));
   {
@@ -939,9 +954,10 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
     CUDA_TRY(eig_prepare(f64));
+    if (tc_apply) CUDA_TRY(eig_apply_tc_prepare());
     std::vector<int> nbs(na);
     for (int i = 0; i < na; i++) nbs[i] = eps[i].nb;
-    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps);
+    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps, tc_apply);
     std::vector<double> hc(n_cum, 0.0);
     std::vector<EigProb> fin(na);   // descriptors after the loop: active = still rotating
     if (rc == CTEBD_OK) {
@@ -955,7 +971,8 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     // launches: every sweep runs both halves' rounds (counted as for one batch)
     const double rounds = hc[3 * na] * (max_nb - 1);
     m->prof.launches[KK_EIG_INNER] += rounds;
-    m->prof.launches[KK_EIG_APPLY] += rounds;
+    m->prof.launches[KK_EIG_APPLY] += rounds * (tc_apply ? 2 : 1);
+    if (tc_apply) m->prof.tc[KK_EIG_APPLY] += rounds * 2;
     for (int i = 0; i < na; i++) {
       // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
       m->prof.flops[KK_EIG_INNER] += hc[3 * i] * 42.0 * (2 * JB);
@@ -990,8 +1007,14 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       {
         // flops and bytes are added after the sweep from the tiles actually updated
         ProfScope ps(m->prof, m->stream, KK_EIG_APPLY, 0, 0);
-        CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
-                     : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
+        if (tc_apply) {
+          m->prof.launches[KK_EIG_APPLY] += 1;   // two launches (phases) per round
+          m->prof.tc[KK_EIG_APPLY] += 2;
+          CUDA_TRY(launch_eig_apply_tc(dep, na, max_nb, max_npad, t, m->tc_err, m->stream));
+        } else {
+          CUDA_TRY(f64 ? launch_eig_apply<double>(dep, na, max_nb, t, m->stream)
+                       : launch_eig_apply<float>(dep, na, max_nb, t, m->stream));
+        }
       }
     }
     CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, m->stream));
@@ -1304,9 +1327,19 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
   // pass 1 already resolved (>= 1024 eps W: their Rayleigh quotients are
   // accurate to second order); block pairs entirely in one such class are
   // skipped outright.
+  // Refine where something is discarded, and where a cutoff is set and pass 1
+  // left directions below its resolution (weights under 1024 eps W, or within
+  // the band of the smallest kept one): their pass-1 weights are mixtures of
+  // everything below ~eps W, so a cutoff smaller than that would otherwise
+  // keep every direction.  Nothing to refine where every direction is kept
+  // and resolved, or where no cutoff applies.
   std::vector<int> ref;
-  for (int a : sel)   // nothing to refine where every direction is kept
-    if ((int)m->h_res[16 * a] < L.ne[a]) ref.push_back(a);
+  for (int a : sel) {
+    const double* res = m->h_res + 16 * a;
+    const bool discarded = (int)res[0] < L.ne[a];
+    const bool unresolved = m->cfg.cutoff > 0 && (int)res[6] < L.ne[a];
+    if (discarded || unresolved) ref.push_back(a);
+  }
   if (ref.empty()) return CTEBD_OK;
   std::vector<const void*> Z2;
   for (int a : ref) Z2.push_back(ws[L.act[a]].bufB);
@@ -1783,6 +1816,86 @@ extern "C" int mps_sketch_stats(const ctebd_mps* m, double* out) {
 }
 
 // operator-Schmidt rank of a gate across a cut between its qubits
+// ---------------------------------------------------------------------------
+// Sec. III.B, Eqs. 9-11: the virtual MPS of a circuit section and the
+// adaptive grouping of its sites by recursive min-cut bipartitioning.
+// ---------------------------------------------------------------------------
+extern "C" int virtual_mps_bonds(const ctebd_gate* gates, int n_gates, int n_qubits, int layer_start, int l_max,
+                                 const int* chi, int chi_max, int* out, int* entangling) {
+  if (!gates && n_gates > 0) return fail(CTEBD_ERR_ARG, "virtual_mps_bonds: null gates");
+  if (n_qubits < 1 || !chi || !out || chi_max < 1 || layer_start < 0)
+    return fail(CTEBD_ERR_ARG, "virtual_mps_bonds: bad arguments");
+  std::vector<long long> E(n_qubits + 1, 0);
+  const long long hi = l_max > 0 ? (long long)layer_start + l_max : (long long)1 << 60;
+  for (int i = 0; i < n_gates; i++) {
+    const ctebd_gate& g = gates[i];
+    if (g.layer <= layer_start || g.layer > hi || g.n_q < 2) continue;
+    int lo = g.q[0];
+    for (int j = 1; j < g.n_q; j++) lo = std::min(lo, g.q[j]);
+    if (lo < 0 || lo + g.n_q > n_qubits) return fail(CTEBD_ERR_ARG, "virtual_mps_bonds: gate out of range");
+    for (int b = lo + 1; b < lo + g.n_q; b++) E[b] += 1;   // bonds the gate spans
+  }
+  for (int b = 0; b <= n_qubits; b++) {
+    if (chi[b] < 1) return fail(CTEBD_ERR_ARG, "virtual_mps_bonds: chi < 1");
+    // min(2^E chi_b, chi_max, 2^min(b, N-b)), saturating
+    const int edge = std::min(b, n_qubits - b);
+    long long v = chi_max;
+    if (edge < 31) v = std::min<long long>(v, 1LL << edge);
+    long long grown = chi[b];
+    for (long long e = 0; e < E[b] && grown < v; e++) grown *= 2;
+    out[b] = (int)std::min(v, grown);
+    if (entangling) entangling[b] = (int)std::min<long long>(E[b], 1 << 30);
+  }
+  return CTEBD_OK;
+}
+
+// 2^size * chi_l * chi_r <= 2^q_max, exactly (Eq. 10 / Eq. 11 in log form)
+static bool group_fits(int size, long long chi_l, long long chi_r, int q_max) {
+  const int room = q_max - size;
+  if (room < 0) return false;
+  if (room >= 62) return true;
+  return chi_l * chi_r <= (1LL << room);
+}
+
+extern "C" int adaptive_grouping(const int* chi_v, int n_qubits, int q_max, double imbalance, int* group_start,
+                                 int cap, int* n_groups) {
+  if (!chi_v || n_qubits < 1 || !group_start || !n_groups || cap < 1 || !(imbalance >= 0.0))
+    return fail(CTEBD_ERR_ARG, "adaptive_grouping: bad arguments");
+  for (int b = 0; b <= n_qubits; b++)
+    if (chi_v[b] < 1) return fail(CTEBD_ERR_ARG, "adaptive_grouping: bond dimension < 1");
+  // segments [lo, hi) of qubits, bounded by bonds lo and hi (the chain ends count as 1)
+  auto bond = [&](int b) -> long long { return (b == 0 || b == n_qubits) ? 1 : chi_v[b]; };
+  std::vector<std::pair<int, int>> stack = {{0, n_qubits}};
+  int count = 0;
+  while (!stack.empty()) {
+    const auto [lo, hi] = stack.back();
+    stack.pop_back();
+    const int size = hi - lo;
+    if (group_fits(size, bond(lo), bond(hi), q_max)) {
+      if (count >= cap) return fail(CTEBD_ERR_ARG, "adaptive_grouping: cap too small");
+      group_start[count++] = lo;
+      continue;
+    }
+    if (size == 1)
+      return fail(CTEBD_ERR_STATE, "adaptive_grouping: site " + std::to_string(lo) +
+                                       " does not fit Q_max with its bonds");
+    // balanced min-cut: parts no larger than (1 + imbalance) * ceil(size / 2)
+    const long long cap_part = (long long)std::floor((1.0 + imbalance) * ((size + 1) / 2) + 1e-9);
+    int best = -1;
+    for (int k = lo + 1; k < hi; k++) {
+      if (k - lo > cap_part || hi - k > cap_part) continue;
+      if (best < 0) { best = k; continue; }
+      const long long a = bond(k), b = bond(best);
+      const int dk = std::abs(2 * k - (lo + hi)), db = std::abs(2 * best - (lo + hi));
+      if (a < b || (a == b && dk < db)) best = k;
+    }
+    stack.push_back({best, hi});   // right part after the left one
+    stack.push_back({lo, best});
+  }
+  *n_groups = count;
+  return CTEBD_OK;
+}
+
 static int gate_osr(int kind, int n_q) {
   if (n_q >= 3) return 4;
   if (kind == CTEBD_SWAP || kind == CTEBD_SQSWAP) return 4;

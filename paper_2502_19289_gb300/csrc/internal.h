@@ -51,6 +51,7 @@ struct EigProb {
   int cut_lo, cut_hi;  // cut_hi > 0: columns sorted by weight, [0, cut_lo) kept and
                        // [cut_hi, npad) discarded for sure; rotations inside either
                        // set are skipped (they move no weight across the cut)
+  void* T;             // npad x npad scratch of the tensor-core round update (FP32)
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -148,6 +149,12 @@ template <typename R>
 cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round,
                              cudaStream_t s);
 int eig_block(bool fp64);  // JB
+// FP32 round update on the tensor cores (two launches: V and the upper G tiles
+// into T, then the G tiles from T); same contract as launch_eig_apply<float>,
+// plus the scratch EigProb::T; a bounded completion wait that expires sets *err.
+cudaError_t launch_eig_apply_tc(const EigProb* d_probs, int n_probs, int max_nb, int max_npad, int round, int* err,
+                                cudaStream_t s);
+cudaError_t eig_apply_tc_prepare();
 // Set the kernels' shared-memory attributes (idempotent); call before any
 // stream capture of the eigen-solve launches.
 cudaError_t eig_prepare(bool fp64);

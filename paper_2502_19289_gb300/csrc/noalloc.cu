@@ -113,7 +113,7 @@ static int na_gemm(NaDesc& d, const GemmProb& p) {
 // Block-Jacobi on G (npad x npad) accumulating into acc; same kernels and
 // stopping rule as the handle path.
 static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor,
-                  double rel_skip) {
+                  double rel_skip, double move_rel) {
   // [0] significant rotations, [1] all rotations, [2] applied flops (the
   // kernels' third counter, unused without pair flags), [3] trace of G
   double* cnt = (double*)(S + NA_OFF_CNT);
@@ -122,6 +122,7 @@ static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor
   e.npad = npad; e.nb = npad / NA_JB; e.active = 1;
   e.off = cnt; e.scale = cnt + 3; e.floor_factor = floor_factor;
   e.rel_skip = rel_skip;   // no pair flags: every tile is updated
+  e.move_rel = move_rel;
   const EigProb* de;
   const size_t mark = d.off;
   if (int rc = d.put(&e, 1, &de)) return rc;
@@ -211,7 +212,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     if (int rc = na_gemm(d, p)) return rc;
   }
   void* V = S + NA_OFF_V;
-  if (int rc = na_eig(d, S, V, npad, 1.0, 4.0)) return rc;
+  if (int rc = na_eig(d, S, V, npad, 1.0, 4.0, 0.0)) return rc;
   double res[8];
   auto select = [&](const void* Vc) -> int {
     if (int rc = na_project(d, S, Vc, m, n, npad, lam_l)) return rc;
@@ -221,15 +222,19 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     sp.rank_cap = std::min(m, n);   // lam_out and site_l_out hold at most min(chi_max, m, n)
     const SelProb* dsp;
     if (int rc = d.put(&sp, 1, &dsp)) return rc;
-    NA_CUDA(launch_select(dsp, 1, chi_max, cutoff, 0.0, 0.0, 1e-12, s));
+    // same truncation parameters as the handle path's FP32 split
+    const double eps32 = 1.1920928955078125e-07;
+    NA_CUDA(launch_select(dsp, 1, chi_max, cutoff, 16.0 * eps32, 1024.0 * eps32, 1e-12, s));
     NA_CUDA(cudaMemcpyAsync(res, S + NA_OFF_RES, sizeof(res), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
     d.off = 0;
     return CTEBD_OK;
   };
   if (int rc = select(V)) return rc;
-  // pass 2 wherever something is discarded (relative thresholds, as the handle path)
-  if ((int)res[0] < n) {
+  // pass 2 wherever something is discarded, or a cutoff is set and pass 1 left
+  // unresolved directions (relative thresholds and the moved-weight stopping
+  // rule of the handle path)
+  if ((int)res[0] < n || (cutoff > 0 && (int)res[6] < n)) {
     NA_CUDA(cudaMemsetAsync(S + NA_OFF_G, 0, (size_t)npad * npad * NA_CPLX, s));
     GemmProb p{};
     p.M = n; p.N = n; p.K = m; p.batch = 1;
@@ -238,7 +243,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     p.C = S + NA_OFF_G; p.ldc = npad;
     p.kw = lam_l; p.kw_shift = 1; p.alpha = 1.0;
     if (int rc = na_gemm(d, p)) return rc;
-    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0)) return rc;
+    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0, 1e-13)) return rc;
     GemmProb q{};
     q.M = n; q.N = n; q.K = n; q.batch = 1;
     q.A = V; q.lda = npad; q.opA = 0;

@@ -118,6 +118,47 @@ def random_structured(n: int, n_layers: int, *, p1: float, p2: float,
     return b.build()
 
 
+# the gate sets of the two random-structured circuit families (Sec. IV.A):
+# Clifford, and the same sets extended by non-Clifford gates (one in two of
+# each set non-Clifford); P(3 pi / 4) carries its angle as the parameter
+PAPER_CLIFFORD_1Q = ((H, 0.0), (X, 0.0), (Y, 0.0), (Z, 0.0))
+PAPER_CLIFFORD_2Q = (CNOT, CY, CZ, SWAP)
+PAPER_NONCLIFFORD_1Q = PAPER_CLIFFORD_1Q + ((T, 0.0), (P, 0.75 * math.pi), (X14, 0.0), (SQW, 0.0))
+PAPER_NONCLIFFORD_2Q = PAPER_CLIFFORD_2Q + (CH, CS, CT, SQSWAP)
+
+
+def paper_random_structured(n: int, n_layers: int, *, clifford: bool, seed: int = 0,
+                            p_two: float = 0.5) -> Circuit:
+    """Random-structured circuit as the paper generates it (Sec. IV.A): every
+    slot of every layer is filled, left to right, with a random one-qubit gate
+    or -- with probability p_two = 0.5, when a right neighbour is still free in
+    the layer -- a random two-qubit gate on the slot and its right neighbour,
+    until all layers are complete.  Gates are drawn uniformly from the
+    Clifford sets {H, X, Y, Z} and {CNOT, C-Y, C-Z, SWAP}, or from those sets
+    extended by {T, P(3 pi/4), X^1/4, sqrt(W)} and {C-H, C-S, C-T, sqrt(SWAP)}
+    (clifford=False).  The control of an asymmetric two-qubit gate is either
+    qubit, uniformly (first listed = control)."""
+    rng = np.random.default_rng(seed)
+    one = PAPER_CLIFFORD_1Q if clifford else PAPER_NONCLIFFORD_1Q
+    two = PAPER_CLIFFORD_2Q if clifford else PAPER_NONCLIFFORD_2Q
+    b = _Builder(n)
+    for _ in range(n_layers):
+        q = 0
+        while q < n:
+            if q + 1 < n and rng.random() < p_two:
+                kind = int(two[rng.integers(len(two))])
+                if rng.random() < 0.5:
+                    b.g2(kind, q, q + 1)
+                else:
+                    b.g2(kind, q + 1, q)
+                q += 2
+            else:
+                kind, param = one[rng.integers(len(one))]
+                b.g1(int(kind), q, float(param))
+                q += 1
+    return b.build()
+
+
 # ---- workload definitions (seed = 1000 * config + sample) -------------------
 @dataclass
 class Workload:
