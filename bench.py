@@ -238,6 +238,169 @@ def method_flops(clusters, chi, log):
     return fm, fu, fs
 
 
+class PlainFP64:
+    """The plain FP64 GPU cluster update, one cluster at a time: complex128
+    merge and unitary with torch, every split a full cuSOLVER SVD
+    (torch.linalg.svd) of the Schmidt-weighted matrix, the same truncation rule
+    and gauge as the library (right-canonical sites, unweighted remainder,
+    renormalised spectra), no batching and no sketch."""
+
+    def __init__(self, torch, sites, lams, device):
+        self.t = torch
+        self.dev = device
+        self.sites = [torch.as_tensor(s, device=device).to(torch.complex128) for s in sites]
+        self.lams = [np.asarray(l, dtype=np.float64).copy() for l in lams]
+        self.logF = 0.0
+
+    def chi(self):
+        return np.array([1] + [int(s.shape[2]) for s in self.sites], dtype=np.int32)
+
+    def apply_1q(self, q, u):
+        ut = self.t.as_tensor(u, dtype=self.t.complex128, device=self.dev)
+        self.sites[q] = self.t.einsum("st,atb->asb", ut, self.sites[q])
+
+    def update(self, q0, k, U, chi_max, cutoff, floor=1e-13):
+        t = self.t
+        th = self.sites[q0]
+        for j in range(1, k):
+            th = t.tensordot(th, self.sites[q0 + j], dims=([th.dim() - 1], [0]))
+        cl, cr = th.shape[0], th.shape[-1]
+        th = t.einsum("st,atb->asb", t.as_tensor(U, dtype=t.complex128, device=self.dev),
+                      th.reshape(cl, 1 << k, cr))
+        lamL = t.as_tensor(self.lams[q0], dtype=t.float64, device=self.dev)
+        R, rdim, fs = th.reshape(-1), cr, []
+        for j in range(k - 1, 0, -1):
+            m, n = cl << j, 2 * rdim
+            Mb = R.reshape(m, n)
+            w = lamL.repeat_interleave(1 << j).to(t.complex128)
+            _, S, Vh = t.linalg.svd(w[:, None] * Mb, full_matrices=False)
+            s = S.double().cpu().numpy()
+            s2 = s * s
+            W = float(s2.sum())
+            r = len(s)
+            if cutoff > 0:
+                tail = np.cumsum(s2[::-1])[::-1]
+                over = np.nonzero(tail[1:] > cutoff * W)[0]
+                r = int(over[-1]) + 2 if len(over) else 1
+            r = max(1, min(r, int(np.sum(s > floor * s[0])), chi_max))
+            kept = float(s2[:r].sum())
+            fs.append(kept / W)
+            self.logF += math.log(kept / W)
+            self.sites[q0 + j] = Vh[:r].reshape(r, 2, rdim).contiguous()
+            self.lams[q0 + j] = s[:r] / math.sqrt(kept)
+            R = (Mb @ Vh[:r].conj().T / math.sqrt(kept)).reshape(-1)
+            rdim = r
+        self.sites[q0] = R.reshape(cl, 2, rdim).contiguous()
+        return fs
+
+
+def mps_overlap(torch, a_sites, b_sites):
+    """<a|b> / (|a| |b|) of two MPS given as lists of (chi, 2, chi) tensors."""
+    def inner(x, y):
+        E = torch.ones((1, 1), dtype=torch.complex128, device=x[0].device)
+        for A, B in zip(x, y):
+            E = torch.einsum("ab,asc,bsd->cd", E, A.conj(), B)
+        return E.reshape(-1)[0]
+    ab = inner(a_sites, b_sites)
+    return float(abs(ab) / math.sqrt(abs(inner(a_sites, a_sites)) * abs(inner(b_sites, b_sites))))
+
+
+def run_compare(args):
+    """The same iterations three ways from one state: the library's FP32 path
+    (batched, tensor cores), the library's FP64 mode (same kernels and
+    batching in complex128 / FP64 Jacobi) and the plain FP64 GPU path
+    (PlainFP64).  Workload: the chi_max = 1024 workload's circuit statistics on
+    an n-qubit state saturated at chi; every arm runs `steps` iterations after
+    one untimed warm-up iteration; device time of the updates with CUDA events.
+    Reports updates/s of every arm and the final fidelity products."""
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import synth
+    device = "cuda:0"
+    w = synth.WORKLOADS[4]
+    n, chi, kmax = args.n, args.chi, args.kmax
+    q_max = kmax + 2 * int(math.log2(chi))
+    c = synth.random_structured(n, w.n_layers, p1=w.p1, p2=w.p2, one_q=w.one_q, two_q=w.two_q, seed=4100)
+    circ = P.Circuit(n, c.gates, c.params)
+    chis, sites, lams = synth.random_right_canonical(n, chi, seed=4100, dtype=np.complex64)
+    stream = torch.cuda.Stream(device=device)
+    out = {}
+    final_sites = {}
+
+    def iterate(step_fn, chi_fn, one_q_fn, start):
+        chi_now = chi_fn()
+        clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, start, chi_now, cfgs["fp32"])
+        used = set(q for cl in clusters for q in range(cl.q0, cl.q0 + cl.k))
+        singles = [(q, P.cluster_unitary(circ.gates, circ.n_gates, P.Cluster(q, 1, start, stop)))
+                   for q in range(n) if q not in used]
+        one_q_fn(clusters, start, stop, singles)
+        Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in clusters]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            step_fn(clusters, Us)
+        e1.record(stream)
+        e1.synchronize()
+        return stop, len(clusters), e0.elapsed_time(e1) / 1e3
+
+    cfgs = {"fp32": P.make_config(n, chi, w.cutoff, q_max, 0, kmax, P.FP32),
+            "fp64": P.make_config(n, chi, w.cutoff, q_max, 0, kmax, P.FP64)}
+    for arm in ("fp32", "fp64", "plain_fp64"):
+        if arm == "plain_fp64":
+            m = PlainFP64(torch, sites, lams, device)
+
+            def step_fn(clusters, Us, m=m):
+                for cl, U in zip(clusters, Us):
+                    m.update(cl.q0, cl.k, U, chi, w.cutoff)
+
+            def one_q_fn(clusters, lo, hi, singles, m=m):
+                for q, u in singles:
+                    m.apply_1q(q, u)
+            chi_fn = m.chi
+            F = lambda m=m: math.exp(m.logF)
+        else:
+            m = P.MPS(cfgs[arm], stream.cuda_stream)
+            m.load(chis, [s.astype(np.complex128) for s in sites], lams)
+
+            def step_fn(clusters, Us, m=m):
+                m.step(clusters, Us)
+
+            def one_q_fn(clusters, lo, hi, singles, m=m):
+                m.apply_singletons(circ.gates, circ.n_gates, clusters, lo, hi)
+            chi_fn = m.bond_dims
+            F = m.fidelity
+        start, _, _ = iterate(step_fn, chi_fn, one_q_fn, 0)       # warm-up iteration
+        updates, dev_s = 0, 0.0
+        for _ in range(args.steps):
+            start, nu, dt = iterate(step_fn, chi_fn, one_q_fn, start)
+            updates += nu
+            dev_s += dt
+        out[arm] = {"updates_per_s": updates / dev_s, "updates": updates, "device_s": dev_s,
+                    "F_final": F(), "chi_max_reached": int(max(chi_fn()))}
+        if arm == "plain_fp64":
+            final_sites[arm] = m.sites
+        else:
+            final_sites[arm] = [torch.as_tensor(m.site(q), device=device) for q in range(n)]
+            m.close()
+        torch.cuda.empty_cache()
+    ov32 = mps_overlap(torch, final_sites["fp32"], final_sites["plain_fp64"])
+    ov64 = mps_overlap(torch, final_sites["fp64"], final_sites["plain_fp64"])
+    line = {"metric": "cluster updates/s at equal final fidelity: FP32 tensor-core path vs plain FP64 GPU path",
+            "unit": "cluster updates/s", "higher_is_better": True, "n_gpus": 1, "dtype": "c64 / c128",
+            "data": "synthetic (seeded circuit + random saturated MPS)",
+            "config": {"workload": f"n={n}, chi_max={chi} (state saturated at chi), chi_max=1024 workload's "
+                                   f"circuit statistics, cutoff 1e-8, k_max={kmax}, Q_max={q_max}; "
+                                   f"{args.steps} timed iterations after 1 warm-up, same state for every arm"},
+            "arms": out,
+            "speedup_fp32_vs_plain": out["fp32"]["updates_per_s"] / out["plain_fp64"]["updates_per_s"],
+            "speedup_fp32_vs_fp64_mode": out["fp32"]["updates_per_s"] / out["fp64"]["updates_per_s"],
+            "abs_dF_fp32_vs_plain": abs(out["fp32"]["F_final"] - out["plain_fp64"]["F_final"]),
+            "abs_dF_fp64_vs_plain": abs(out["fp64"]["F_final"] - out["plain_fp64"]["F_final"]),
+            "overlap_fp32_vs_plain": ov32, "overlap_fp64_vs_plain": ov64}
+    print(json.dumps(line))
+
+
 def aggregate(dev_s: float, wall_s: float, units: int, device=None):
     """Whole-job figures over all ranks: max of the times, sum of the units.
 
@@ -548,12 +711,16 @@ def main():
                     help="largest cluster (Q_max = kmax + 2 log2 chi); 6 lets k = 3..6 clusters form")
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2"],
-                    help="cfg4: the headline (saturated chi=1024, full split); cfg2: full vs sketched split")
+    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "compare"],
+                    help="cfg4: the headline (saturated chi=1024, full split); cfg2: full vs sketched split; "
+                         "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations")
     ap.add_argument("--layers", type=int, default=0, help="cfg2 mode: circuit depth (default: the workload's 50)")
     args = ap.parse_args()
     if args.workload == "cfg2":
         run_cfg2(args)
+        return
+    if args.workload == "compare":
+        run_compare(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -282,11 +282,13 @@ int mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, floa
    for validation.  Errors: ARG, CUDA, TIMEOUT (bounded completion wait). */
 int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* stream);
 
-/* Tensor-core policy for the FP32 complex GEMMs (merge, U on clusters with
-   2^k > 16, Gram, projections, sketches), process-wide: 0 never; 1 (default)
-   batches above 2 GFLOP of work, whose problems with fewer than 64 rows run on
-   the CUDA cores; 2 always.  FP64 GEMMs always use the CUDA cores; U on
-   clusters with 2^k <= 16 is a streaming kernel in every mode. */
+/* Tensor-core policy for the FP32 complex products, process-wide: 0 never;
+   1 (default) the GEMMs (merge, U on clusters with 2^k > 16, Gram,
+   projections, sketches) of batches above 2 GFLOP of work, whose problems
+   with fewer than 64 rows run on the CUDA cores; 2 always, including the
+   Jacobi round updates of the eigen-solve (3xTF32 tile products on tcgen05).
+   FP64 products always use the CUDA cores; U on clusters with 2^k <= 16 is a
+   streaming kernel in every mode. */
 int ctebd_set_tensor_cores(int mode);
 
 /* Eigen-solve sweep loop on the device (not in the paper): with per-launch

@@ -398,6 +398,8 @@ struct ctebd_mps {
   uint64_t nstep = 0;
   float* mlp = nullptr;            // rank predictor parameters (device)
   int* tc_err = nullptr;           // tensor-core completion-wait timeout flag (device)
+  double* eig_scr = nullptr;       // eigen-solve counters and pair flags (high-water)
+  size_t eig_scr_cap = 0;          // in doubles
   cudaStream_t side = nullptr;     // second branch of the device-side sweep graphs
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* arena = nullptr;
@@ -493,6 +495,7 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   if (m->arena) cudaFree(m->arena);
   if (m->mlp) cudaFree(m->mlp);
   if (m->tc_err) cudaFree(m->tc_err);
+  if (m->eig_scr) cudaFree(m->eig_scr);
   if (m->h_res) cudaFreeHost(m->h_res);
   m->stage.release();
   m->prof.release();
@@ -514,6 +517,22 @@ static int g_tc_mode = 1;
 extern "C" int ctebd_set_tensor_cores(int mode) {
   if (mode < 0 || mode > 2) return fail(CTEBD_ERR_ARG, "ctebd_set_tensor_cores: mode 0, 1 or 2");
   g_tc_mode = mode;
+  return CTEBD_OK;
+}
+
+// grow the eigen-solve scratch to at least n doubles (synchronises only when it grows)
+static int ensure_eig_scratch(ctebd_mps* m, size_t n) {
+  if (n <= m->eig_scr_cap) return CTEBD_OK;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (m->eig_scr) CUDA_TRY(cudaFree(m->eig_scr));
+  m->eig_scr = nullptr;
+  m->eig_scr_cap = 0;
+  const size_t want = n + n / 2 + 1024;
+  if (cudaMalloc(&m->eig_scr, sizeof(double) * want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CTEBD_ERR_OOM, "eigen-solve scratch");
+  }
+  m->eig_scr_cap = want;
   return CTEBD_OK;
 }
 
@@ -905,13 +924,20 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     max_nb = std::max(max_nb, L.nbv[sel[i]]);
   }
   const int maxh = std::max(1, max_nb / 2);
-  // FP32 round updates on the tensor cores: policy of ctebd_set_tensor_cores
-  // (1: eigenproblems of at least 256 columns; 2: always; 0: never)
-  const bool tc_apply = !f64 && (g_tc_mode == 2 || (g_tc_mode == 1 && max_npad >= 256));
+  // FP32 round updates on the tensor cores only when the tensor-core policy
+  // forces every FP32 product onto them (ctebd_set_tensor_cores(2)): measured
+  // on 2048-wide batches, the CUDA-core round update is faster (the tile
+  // products' operand staging is latency-bound at K = 64)
+  const bool tc_apply = !f64 && g_tc_mode == 2;
   // per problem: 3 counters (zeroed every sweep), the trace, then maxh pair flags
-  double* d_off = nullptr;
+  // per problem: 3 counters, the trace, the pair flags; then the device-side
+  // loop's cumulative counters (3 per problem + the sweep count), in the
+  // handle's high-water scratch (no allocation once it has grown)
   const size_t n_dbl = 4 * (size_t)na + ((size_t)na * maxh + 1) / 2;
-  CUDA_TRY(cudaMallocAsync(&d_off, sizeof(double) * n_dbl, m->stream));
+  const size_t n_cum = 3 * (size_t)na + 1;
+  TRY(ensure_eig_scratch(m, n_dbl + n_cum));
+  double* d_off = m->eig_scr;
+  double* d_cum = m->eig_scr + n_dbl;
   int* d_flag = reinterpret_cast<int*>(d_off + 4 * na);
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
@@ -948,9 +974,6 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   };
   if (g_sweep_graphs && !m->prof.on) {
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
-    double* d_cum = nullptr;
-    const size_t n_cum = 3 * (size_t)na + 1;
-    CUDA_TRY(cudaMallocAsync(&d_cum, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
     CUDA_TRY(eig_prepare(f64));
@@ -965,8 +988,6 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       CUDA_TRY(cudaMemcpyAsync(fin.data(), dep, sizeof(EigProb) * na, cudaMemcpyDeviceToHost, m->stream));
       CUDA_TRY(cudaStreamSynchronize(m->stream));
     }
-    cudaFreeAsync(d_cum, m->stream);
-    cudaFreeAsync(d_off, m->stream);
     TRY(rc);
     // launches: every sweep runs both halves' rounds (counted as for one batch)
     const double rounds = hc[3 * na] * (max_nb - 1);
@@ -1035,7 +1056,6 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     m->stage.reset();
     TRY(m->stage.push(eps.data(), eps.size(), &dep));
   }
-  CUDA_TRY(cudaFreeAsync(d_off, m->stream));
   int left = 0;
   for (int i = 0; i < na; i++) left += eps[i].active ? 1 : 0;
   if (left) return not_converged(left);

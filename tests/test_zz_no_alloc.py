@@ -53,10 +53,15 @@ def _case(P, torch, seed, chi, cutoff, n=4, q0=1, chi_max=None, steep=False):
     np.testing.assert_allclose(lam.cpu().numpy()[:r], lam_ref, atol=1e-5)
     A = A.cpu().numpy()[: cl * 2 * r].reshape(cl, 2, r)
     B = B.cpu().numpy()[: r * 2 * cr].reshape(r, 2, cr)
-    got = np.einsum("asm,mtb->astb", A, B)          # gauge-invariant product
-    want = np.einsum("asm,mtb->astb", A_ref, B_ref)
-    scale = max(float(np.max(np.abs(want))), 1e-30)
-    np.testing.assert_allclose(got, want, atol=1e-5 * max(scale, 1.0))
+    # the kept part of the cluster tensor, diag(lambda_l) A B: independent of the
+    # basis chosen inside the kept space (rows of tiny Schmidt weight are resolved
+    # only relative to the weighted norm, so the unweighted product is not
+    # compared); directions at a chi_max cut inside a flat spectrum are resolved
+    # to the split's 1e-5 weight tolerance, so the two paths agree to that level
+    w = np.asarray(lams[q0], dtype=np.float64)[:, None, None, None]
+    got = w * np.einsum("asm,mtb->astb", A, B)
+    want = w * np.einsum("asm,mtb->astb", A_ref, B_ref)
+    np.testing.assert_allclose(got, want, atol=2e-5 * float(np.max(np.abs(want))))
     Bm = B.reshape(r, -1)
     np.testing.assert_allclose(Bm @ Bm.conj().T, np.eye(r), atol=1e-5)
     return cl, cr, r
