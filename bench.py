@@ -18,6 +18,7 @@ ranks / max time over ranks, scaling "weak".
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -33,6 +34,39 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cluster updates/s and TFLOP/s (% TC peak) at χ=1024 vs plain FP64 GPU path"
 UNIT = "cluster updates/s"
+
+# DRAM traffic of the FP32 round update (k_eig_apply_f32) per algorithmic flop,
+# from one ncu capture of the small case of run_apply_traffic (inputs larger
+# than L2).  The figure holds for the kernel source it was taken on: the
+# reported traffic is null once that text changes.  The round update reads and
+# writes each tile once per 64^3 complex product, so its bytes grow with its
+# flops and the per-flop figure scales to any launch.
+APPLY_TRAFFIC = {
+    "bytes_per_flop": (69243392 + 27080448) / 5779750912.0,
+    "source_sha256": "c44bb9a37c7691cb792bbd36c8dd8912ab3e939cb38920bb7a6e8af5dea6562d",
+    "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first k_eig_apply_f32 launch of "
+               "'bench.py --workload apply-traffic --n 24' on a GB300 (7 problems, widths 2..2048): "
+               "69,243,392 + 27,080,448 B for 5.780e9 algorithmic flops, scaled to this launch's flops",
+}
+
+
+def apply_kernel_digest() -> str:
+    """sha256 of the FP32 round-update kernel's source text (comment, tile
+    constants and kernel body)."""
+    src = open(os.path.join(ROOT, "paper_2502_19289_gb300", "csrc", "kernels.cu")).read()
+    a = src.index("// FP32 apply, one 64 x 64")
+    b = src.index("\n}\n", src.index("k_eig_apply_f32(const EigProb*", a)) + 3
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
+def apply_traffic_per_launch(flops_per_launch: float):
+    """(bytes, note) for a round-update launch of the given algorithmic flops."""
+    t = APPLY_TRAFFIC
+    if t["bytes_per_flop"] is None:
+        return None, "no capture"
+    if t["source_sha256"] != apply_kernel_digest():
+        return None, "kernel changed since the capture"
+    return t["bytes_per_flop"] * flops_per_launch, t["capture"]
 
 
 def peaks():
@@ -401,6 +435,42 @@ def run_compare(args):
     print(json.dumps(line))
 
 
+def run_apply_traffic(args):
+    """Small case for the dominant kernel's DRAM traffic per algorithmic flop:
+    one saturated chi = 1024 iteration on n qubits (host-generated state,
+    host-driven sweep rounds so that every launch is visible to a profiler).
+    Prints the eigenproblems of the first eigen-solve and the algorithmic flops
+    of its first round update, in which every pair of column blocks rotates:
+    one 64^3 complex product per V tile and two per upper G tile.  Captured as
+
+        python bench.py --workload apply-traffic --n 24 &&
+        ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+            --clock-control none -k regex:k_eig_apply_f32 -c 1 --csv
+            python bench.py --workload apply-traffic --n 24"""
+    import paper_2502_19289_gb300 as P
+    import synth
+    n = args.n
+    if args.tensor_cores is not None:   # 2: the Jacobi round updates on tcgen05 as well
+        P.set_tensor_cores(args.tensor_cores)
+    w = synth.WORKLOADS[4]
+    cfg = P.make_config(n, 1024, w.cutoff, 24, 0, 4, P.FP32)
+    c = synth.random_structured(n, w.n_layers, p1=w.p1, p2=w.p2, one_q=w.one_q, two_q=w.two_q, seed=4000)
+    circ = P.Circuit(n, c.gates, c.params)
+    chis, sites, lams = synth.random_right_canonical(n, 1024, seed=4000, dtype=np.complex64)
+    mps = P.MPS(cfg)
+    mps.load(chis, sites, lams)
+    P.set_sweep_graphs(False)
+    clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, 0, mps.bond_dims(), cfg)
+    Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in clusters]
+    mps.step(clusters, Us)
+    log = mps.split_log()
+    level1 = [row for row in log if int(row[2]) == int(row[0]) + int(row[1]) - 1]
+    h = [((int(row[9]) + 63) // 64 * 64) // 64 for row in level1]   # pairs of 32-wide blocks
+    flops = sum(8.0 * 64 ** 3 * (2 * (x * (x + 1) // 2) + x * x) for x in h)
+    print(json.dumps({"problems": len(h), "widths": sorted(set(int(r[9]) for r in level1)),
+                      "first_round_flops": flops, "source_sha256": apply_kernel_digest()}))
+
+
 def aggregate(dev_s: float, wall_s: float, units: int, device=None):
     """Whole-job figures over all ranks: max of the times, sum of the units.
 
@@ -606,31 +676,39 @@ def cpu_baseline(seconds=12.0, chi=128, nsites=16, workers=None):
 
 def run_cfg2(args):
     """Sketched split (randomized range finder + CholeskyQR + Rayleigh-Ritz, with
-    the tail check) against the full split on the cfg2 workload: n=100, 50
-    layers of random-structured Clifford+T (10% T, 10% long-range pairs),
-    chi_max=256, cutoff 1e-10, k_max=6, from |0...0> through the whole circuit.
+    the tail check) against the full split, from |0...0> through the circuit.
+
+    ``--workload cfg2``: n=100, 50 layers of random-structured Clifford+T (10% T,
+    10% long-range pairs), chi_max=256, cutoff 1e-10, k_max=6.
+    ``--workload sketch-cfg4``: the cfg4 gate statistics (20% T, chi_max=1024,
+    cutoff 1e-8, k_max=4) on ``--n`` qubits (default 100) for ``--layers``
+    layers (default 30): the growing phase, where the bonds climb to chi_max.
     Three modes: full split; sketch sized by the Eq. 9 bound; sketch sized by
-    the learned rank predictor (trained here on cfg2-shaped circuits of 40
-    qubits).  Device time of the cluster updates (CUDA events on the library's
-    stream); the modes must agree on log F and the bond dimensions."""
+    the learned rank predictor (trained in the same run on six smaller circuits
+    of the same gate statistics).  Device time of the cluster updates (CUDA
+    events on the library's stream) and wall time; the modes must agree on log
+    F and the bond dimensions."""
     import torch
 
     import paper_2502_19289_gb300 as P
     import paper_2502_19289_gb300.rank_model as R
     import synth
-    w = synth.WORKLOADS[2]
-    if args.layers:   # same gate statistics, deeper circuit (bonds grow towards chi_max)
+    base = 4 if args.workload == "sketch-cfg4" else 2
+    w = synth.WORKLOADS[base]
+    if base == 4:
+        w = synth.reduced(4, args.n, args.layers or 30)
+    elif args.layers:   # same gate statistics, deeper circuit (bonds grow towards chi_max)
         w = synth.reduced(2, w.n_qubits, args.layers)
     n, chi, over = w.n_qubits, w.chi_max, 8
     q_max = w.k_max + 2 * int(math.log2(chi))
-    c = w.circuit(0, 2)
+    c = w.circuit(0, base)
     stream = torch.cuda.Stream()
 
     t0 = time.perf_counter()
-    small = synth.reduced(2, 40, 60)
+    small = synth.reduced(base, 40, 60 if base == 2 else 22)
     Xs, rs, bs = [], [], []
     for seed in range(1, 7):
-        cc = small.circuit(seed, 2)
+        cc = small.circuit(seed, base)
         X, r, b = R.collect((cc.gates, cc.params), small.n_qubits, chi, w.cutoff, q_max, w.k_max,
                             stream.cuda_stream)
         Xs.append(X); rs.append(r); bs.append(b)
@@ -674,7 +752,7 @@ def run_cfg2(args):
         out = {"updates_per_s": updates / (dev_ms / 1000.0), "e2e_updates_per_s": updates / wall,
                "updates": updates, "device_s": dev_ms / 1000.0, "logF": float(math.log(mps.fidelity())),
                "splits": splits, "sketched": sk, "fell_back": fb, "eigen_work_sum_ne3": work,
-               "max_chi": int(max(mps.bond_dims()))}
+               "max_chi": int(max(mps.bond_dims())), "wall_s": wall}
         dims = list(mps.bond_dims())
         mps.close()
         return out, dims
@@ -682,17 +760,26 @@ def run_cfg2(args):
     full, d_full = run(0, False)
     eq9, d_eq9 = run(over, False)
     learned, d_l = run(over, True)
-    line = {"metric": "cluster updates/s, cfg2 workload: full split vs sketched split (Eq. 9 and learned sizes)",
+    if base == 4:
+        desc = (f"cfg4 gate statistics from |0...0>: n={n}, {w.n_layers}-layer random-structured Clifford+T "
+                f"(20% T), chi_max=1024, cutoff 1e-8, k_max=4, Q_max={q_max}, sketch oversampling 8")
+        trained = f"trained on 6 cfg4-shaped circuits (n=40, 22 layers)"
+    else:
+        desc = (f"cfg2: n=100, {w.n_layers}-layer random-structured Clifford+T (10% T, 10% long-range pairs), "
+                f"chi_max=256, cutoff 1e-10, k_max=6, Q_max={q_max}, sketch oversampling 8")
+        trained = "trained on 6 cfg2-shaped circuits (n=40, 60 layers)"
+    line = {"metric": f"cluster updates/s, {'cfg4 growing phase' if base == 4 else 'cfg2 workload'}: "
+                      "full split vs sketched split (Eq. 9 and learned sizes)",
             "unit": "cluster updates/s", "higher_is_better": True, "n_gpus": 1, "dtype": "c64",
             "data": "synthetic (seeded circuit from |0...0>)",
-            "config": {"workload": f"cfg2: n=100, {w.n_layers}-layer random-structured Clifford+T (10% T, 10% "
-                                   "long-range pairs), chi_max=256, cutoff 1e-10, k_max=6, Q_max=22, sketch "
-                                   "oversampling 8",
-                       "rank_model": f"trained on 6 cfg2-shaped circuits (n=40, 60 layers), {len(X)} splits, "
+            "config": {"workload": desc,
+                       "rank_model": f"{trained}, {len(X)} splits, "
                                      f"loss {hist[0]:.3f} -> {hist[-1]:.3f}, {train_s:.1f} s"},
             "modes": {"full": full, "sketch_eq9": eq9, "sketch_learned": learned},
             "speedup_eq9": eq9["updates_per_s"] / full["updates_per_s"],
             "speedup_learned": learned["updates_per_s"] / full["updates_per_s"],
+            "wall_speedup_eq9": full["wall_s"] / eq9["wall_s"],
+            "wall_speedup_learned": full["wall_s"] / learned["wall_s"],
             "agreement": {"max_abs_dlogF": max(abs(eq9["logF"] - full["logF"]),
                                               abs(learned["logF"] - full["logF"])),
                           "bond_dims_equal": d_full == d_eq9 == d_l}}
@@ -705,22 +792,33 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=500)
+    ap.add_argument("--n", type=int, default=None,
+                    help="qubits (default: 500 for cfg4, 60 for compare, 24 for apply-traffic, 100 for sketch-cfg4)")
     ap.add_argument("--chi", type=int, default=1024)
     ap.add_argument("--kmax", type=int, default=4,
                     help="largest cluster (Q_max = kmax + 2 log2 chi); 6 lets k = 3..6 clusters form")
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "compare"],
-                    help="cfg4: the headline (saturated chi=1024, full split); cfg2: full vs sketched split; "
+    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "compare", "apply-traffic"],
+                    help="cfg4: the headline (saturated chi=1024, full split); cfg2, sketch-cfg4: full vs "
+                         "sketched split (cfg2, and cfg4's growing phase); "
                          "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations")
-    ap.add_argument("--layers", type=int, default=0, help="cfg2 mode: circuit depth (default: the workload's 50)")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
+                    help="apply-traffic mode: tensor-core policy (0 never, 1 size policy, 2 always, "
+                         "including the Jacobi round updates)")
+    ap.add_argument("--layers", type=int, default=0,
+                    help="cfg2 / sketch-cfg4: circuit depth (default: 50 / 30)")
     args = ap.parse_args()
-    if args.workload == "cfg2":
+    if args.n is None:
+        args.n = {"compare": 60, "apply-traffic": 24, "sketch-cfg4": 100}.get(args.workload, 500)
+    if args.workload in ("cfg2", "sketch-cfg4"):
         run_cfg2(args)
         return
     if args.workload == "compare":
         run_compare(args)
+        return
+    if args.workload == "apply-traffic":
+        run_apply_traffic(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -785,8 +883,11 @@ def main():
                 "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1)}
     elif dom["flops"] > 0:
         achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
+        traffic, t_note = (apply_traffic_per_launch(dom["flops"] / max(dom["launches"], 1))
+                           if dom_name == "eig_apply" else (None, "no capture of this kernel"))
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch", "traffic_source": t_note,
                 "peak_source": mp["fp32_source"] + f"; {mp['n_sm']} SMs",
                 "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1)}
     else:

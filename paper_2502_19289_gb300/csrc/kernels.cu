@@ -439,9 +439,14 @@ __global__ void __launch_bounds__(256) k_eig_apply(const EigProb* __restrict__ p
 // owns 8 rows x 4 columns of the tile: rows 16 w + rg + 2 i (warp w, half-warp
 // rg, i < 8) and columns 4 cg .. 4 cg + 3 (cg = lane mod 16), so a k step
 // reads 8 broadcast values of the left operand and two 16-byte vectors of the
-// right one for 32 complex FMAs.  Tiles arrive by 16-byte cp.async copies
-// into rows padded to 66 elements (16-byte aligned, and the two half-warps'
-// rows fall in different banks); J_P is fetched while T is written back.
+// right one for 32 complex multiply-adds.  Tiles arrive by 16-byte cp.async
+// copies into rows padded to 66 elements (16-byte aligned, and the two
+// half-warps' rows fall in different banks); J_P is fetched while T is
+// written back.  By default (APPLY_GAUSS) each complex multiply-add takes
+// three real FMAs (Gauss's product) instead of four, applied to J - I.
+#ifndef APPLY_GAUSS
+#define APPLY_GAUSS 1
+#endif
 namespace {
 constexpr int AP_D = 64, AP_LD = 66, AP_THREADS = 128;
 
@@ -454,6 +459,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 }  // namespace
 
+template <bool GAUSS>
 __global__ void __launch_bounds__(AP_THREADS, 3) k_eig_apply_f32(const EigProb* __restrict__ probs, int round) {
   constexpr int JB = 32, D = AP_D, LD = AP_LD;
   const EigProb P = probs[blockIdx.y];
@@ -500,28 +506,83 @@ __global__ void __launch_bounds__(AP_THREADS, 3) k_eig_apply_f32(const EigProb* 
   }
   cp_async_wait_all();
   __syncthreads();
+  if (GAUSS && fq) {   // J_Q - I: the product runs in the form X + X (J - I)
+    if (t < D) S1[t * LD + t].x -= 1.f;
+    __syncthreads();
+  }
   const int w = t >> 5, lane = t & 31, rg = lane >> 4, cg = lane & 15;
   const int r0 = 16 * w + rg, c0 = 4 * cg;
   float2 acc[8][4];
-  if (fq) {
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll 2
-    for (int k = 0; k < D; k++) {            // T = X_tile J_Q
-      float2 a[8], b[4];
-#pragma unroll
-      for (int i = 0; i < 8; i++) a[i] = S0[(r0 + 2 * i) * LD + k];
-      const float4 b01 = *reinterpret_cast<const float4*>(S1 + k * LD + c0);
-      const float4 b23 = *reinterpret_cast<const float4*>(S1 + k * LD + c0 + 2);
-      b[0] = make_float2(b01.x, b01.y); b[1] = make_float2(b01.z, b01.w);
-      b[2] = make_float2(b23.x, b23.y); b[3] = make_float2(b23.z, b23.w);
+  // out = base + A B over k < 64, thread block 8 rows x 4 columns.  GAUSS:
+  // three real products per complex multiply-add -- t1 = sum ax bx, t2 =
+  // sum ay by, t3 = sum (ax + ay)(bx + by); re = t1 - t2, im = t3 - t1 - t2 --
+  // with A B = X (J - I), whose rounding scales with |J - I|; otherwise the
+  // four-product complex FMA of A B = X J.
+  auto product = [&](auto loadA, auto loadB, const float2* base) {
+    if constexpr (GAUSS) {
+      float t1[8][4], t2[8][4], t3[8][4];
 #pragma unroll
       for (int i = 0; i < 8; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < 4; j++) t1[i][j] = t2[i][j] = t3[i][j] = 0.f;
+#pragma unroll 2
+      for (int k = 0; k < D; k++) {
+        float2 a[8], b[4];
+        float as[8], bs[4];
+        loadA(k, a);
+        loadB(k, b);
+#pragma unroll
+        for (int i = 0; i < 8; i++) as[i] = a[i].x + a[i].y;
+#pragma unroll
+        for (int j = 0; j < 4; j++) bs[j] = b[j].x + b[j].y;
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            t1[i][j] = fmaf(a[i].x, b[j].x, t1[i][j]);
+            t2[i][j] = fmaf(a[i].y, b[j].y, t2[i][j]);
+            t3[i][j] = fmaf(as[i], bs[j], t3[i][j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const float2 x = base[(r0 + 2 * i) * LD + c0 + j];
+          acc[i][j] = make_float2(x.x + (t1[i][j] - t2[i][j]), x.y + ((t3[i][j] - t1[i][j]) - t2[i][j]));
+        }
+    } else {
+      (void)base;
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int k = 0; k < D; k++) {
+        float2 a[8], b[4];
+        loadA(k, a);
+        loadB(k, b);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+      }
     }
+  };
+  auto rowsB = [&](const float2* Sb) {   // row k of B, columns c0 .. c0 + 3, two 16-byte loads
+    return [=](int k, float2 (&b)[4]) {
+      const float4 b01 = *reinterpret_cast<const float4*>(Sb + k * LD + c0);
+      const float4 b23 = *reinterpret_cast<const float4*>(Sb + k * LD + c0 + 2);
+      b[0] = make_float2(b01.x, b01.y); b[1] = make_float2(b01.z, b01.w);
+      b[2] = make_float2(b23.x, b23.y); b[3] = make_float2(b23.z, b23.w);
+    };
+  };
+  if (fq) {                                    // T = X_tile J_Q
+    product([&](int k, float2 (&a)[8]) {
+#pragma unroll
+              for (int i = 0; i < 8; i++) a[i] = S0[(r0 + 2 * i) * LD + k];
+            },
+            rowsB(S1), S0);
   } else {
 #pragma unroll
     for (int i = 0; i < 8; i++)
@@ -544,25 +605,16 @@ __global__ void __launch_bounds__(AP_THREADS, 3) k_eig_apply_f32(const EigProb* 
     }
     cp_async_wait_all();
     __syncthreads();
-    if (fp) {
+    if (GAUSS && fp) {                         // J_P - I
+      if (t < D) S1[t * LD + t].x -= 1.f;
+      __syncthreads();
+    }
+    if (fp) {                                  // Y = J_P^H T
+      product([&](int k, float2 (&a)[8]) {
 #pragma unroll
-      for (int i = 0; i < 8; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int k = 0; k < D; k++) {          // Y = J_P^H T
-        float2 a[8], b[4];
-#pragma unroll
-        for (int i = 0; i < 8; i++) a[i] = cconj(S1[k * LD + r0 + 2 * i]);
-        const float4 b01 = *reinterpret_cast<const float4*>(S0 + k * LD + c0);
-        const float4 b23 = *reinterpret_cast<const float4*>(S0 + k * LD + c0 + 2);
-        b[0] = make_float2(b01.x, b01.y); b[1] = make_float2(b01.z, b01.w);
-        b[2] = make_float2(b23.x, b23.y); b[3] = make_float2(b23.z, b23.w);
-#pragma unroll
-        for (int i = 0; i < 8; i++)
-#pragma unroll
-          for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
-      }
+                for (int i = 0; i < 8; i++) a[i] = cconj(S1[k * LD + r0 + 2 * i]);
+              },
+              rowsB(S0), S0);
     }
   }
 #pragma unroll
@@ -670,7 +722,7 @@ cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, in
     static_assert(D == AP_D, "FP32 apply tile");
     const size_t sm = 2 * sizeof(float2) * AP_D * AP_LD;
     eig_prepare(false);
-    k_eig_apply_f32<<<dim3(h * (h + 1) / 2 + h * h, n_probs), AP_THREADS, sm, s>>>(d_probs, round);
+    k_eig_apply_f32<APPLY_GAUSS != 0><<<dim3(h * (h + 1) / 2 + h * h, n_probs), AP_THREADS, sm, s>>>(d_probs, round);
   } else {
     const size_t sm_apply = 2 * sizeof(CT) * D * LD;
     k_eig_apply<R><<<dim3(h * (h + 1) / 2 + h * h, n_probs), 256, sm_apply, s>>>(d_probs, round);
@@ -686,7 +738,7 @@ cudaError_t eig_prepare(bool fp64) {
     static bool attr = false;
     if (!attr) {
       const size_t sm = 2 * sizeof(float2) * AP_D * AP_LD;
-      cudaFuncSetAttribute(k_eig_apply_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_eig_apply_f32<APPLY_GAUSS != 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       attr = true;
     }
   }
