@@ -36,17 +36,18 @@ METRIC = "cluster updates/s and TFLOP/s (% TC peak) at χ=1024 vs plain FP64 GPU
 UNIT = "cluster updates/s"
 
 # DRAM traffic of the FP32 round update (k_eig_apply_f32) per algorithmic flop,
-# from one ncu capture of the small case of run_apply_traffic (inputs larger
-# than L2).  The figure holds for the kernel source it was taken on: the
-# reported traffic is null once that text changes.  The round update reads and
-# writes each tile once per 64^3 complex product, so its bytes grow with its
-# flops and the per-flop figure scales to any launch.
+# from one ncu capture of run_apply_traffic at n = 60 (G and V of the launch
+# about 1 GB, eight times L2).  The figure holds for the kernel source it was
+# taken on: the reported traffic is null once that text changes.  The round
+# update reads and writes each tile once per 64^3 complex product, so its bytes
+# grow with its flops and the per-flop figure scales to any launch.
 APPLY_TRAFFIC = {
-    "bytes_per_flop": (69243392 + 27080448) / 5779750912.0,
+    "bytes_per_flop": (475024640 + 552518400) / 39868956672.0,
     "source_sha256": "c44bb9a37c7691cb792bbd36c8dd8912ab3e939cb38920bb7a6e8af5dea6562d",
     "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first k_eig_apply_f32 launch of "
-               "'bench.py --workload apply-traffic --n 24' on a GB300 (7 problems, widths 2..2048): "
-               "69,243,392 + 27,080,448 B for 5.780e9 algorithmic flops, scaled to this launch's flops",
+               "'bench.py --workload apply-traffic --n 60' on a GB300 (15 problems, widths up to 2048, "
+               "about 1 GB of G and V): 475,024,640 + 552,518,400 B for 3.987e10 algorithmic flops, "
+               "scaled to this launch's flops",
 }
 
 
@@ -443,10 +444,10 @@ def run_apply_traffic(args):
     of its first round update, in which every pair of column blocks rotates:
     one 64^3 complex product per V tile and two per upper G tile.  Captured as
 
-        python bench.py --workload apply-traffic --n 24 &&
+        python bench.py --workload apply-traffic --n 60 &&
         ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
             --clock-control none -k regex:k_eig_apply_f32 -c 1 --csv
-            python bench.py --workload apply-traffic --n 24"""
+            python bench.py --workload apply-traffic --n 60"""
     import paper_2502_19289_gb300 as P
     import synth
     n = args.n
@@ -469,6 +470,161 @@ def run_apply_traffic(args):
     flops = sum(8.0 * 64 ** 3 * (2 * (x * (x + 1) // 2) + x * x) for x in h)
     print(json.dumps({"problems": len(h), "widths": sorted(set(int(r[9]) for r in level1)),
                       "first_round_flops": flops, "source_sha256": apply_kernel_digest()}))
+
+
+def run_cfg5(args):
+    """cfg5: independent random-structured Clifford+T circuits (n ~ U[50, 300],
+    layers ~ U[40, 100], T density ~ U[5%, 25%] of the one-qubit gates,
+    CNOT/CZ on nearest-neighbour bonds with p = 0.3), chi_max = 1024, cutoff
+    1e-8, k_max = 4, from |0...0>.  All circuits are packed side by side on one
+    MPS and advance together: every iteration steps the clusters of all
+    unfinished circuits in the same batched launches (FP32 path).  Timed: the
+    whole packed simulation, wall clock (host partition included).  Then every
+    circuit runs alone in the library's FP64 mode, and its final bond
+    dimensions, fidelity product and state are compared with its slice of the
+    packed run."""
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import synth
+    rng = np.random.default_rng(5000)
+    circs, spec = [], []
+    for i in range(args.circuits):
+        n = int(rng.integers(50, 301))
+        layers = int(rng.integers(40, 101))
+        t = float(rng.uniform(0.05, 0.25))
+        circs.append(synth.random_structured(n, layers, p1=0.5, p2=0.3,
+                                             one_q={synth.T: t, synth.H: (1 - t) / 2, synth.S: (1 - t) / 2},
+                                             two_q=(synth.CNOT, synth.CZ), seed=5000 + i))
+        spec.append((n, layers, t))
+    k_max, chi, cut = 4, 1024, 1e-8
+    q_max = k_max + 2 * 10
+    stream = torch.cuda.Stream()
+    packed = [(c.n_qubits, c.gates, c.params) for c in circs]
+    cfg = P.make_config(1, chi, cut, q_max, 0, k_max, P.FP32)
+    warm, _ = P.simulate_packed(packed[:2], cfg, stream.cuda_stream)   # untimed: first launches
+    warm.close()
+    counts = {"updates": 0, "iterations": 0}
+
+    def count(cl):
+        counts["updates"] += len(cl)
+        counts["iterations"] += 1
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mps, pk = P.simulate_packed(packed, cfg, stream.cuda_stream, callback=count)
+    stream.synchronize()
+    wall = time.perf_counter() - t0
+    chis = mps.bond_dims()
+    logF_packed = float(math.log(mps.fidelity()))
+    rows, logF_sum = [], 0.0
+    t64 = 0.0
+    for c, off in zip(circs, pk.offsets):
+        n = c.n_qubits
+        cfg64 = P.make_config(n, chi, cut, q_max, 0, k_max, P.FP64)
+        a = time.perf_counter()
+        ref = P.simulate(P.Circuit(n, c.gates, c.params), cfg64, stream.cuda_stream)
+        t64 += time.perf_counter() - a
+        lf64 = float(math.log(ref.fidelity()))
+        logF_sum += lf64
+        prof64 = list(ref.bond_dims())
+        prof32 = list(chis[off:off + n + 1])
+        a_sites = [torch.as_tensor(mps.site(off + q)).to(torch.complex128) for q in range(n)]
+        b_sites = [torch.as_tensor(ref.site(q)).to(torch.complex128) for q in range(n)]
+        ov = mps_overlap(torch, a_sites, b_sites)
+        # the circuit's own fidelity product inside the packed run: its splits' f
+        rows.append({"n": n, "max_chi": max(prof64), "chi_profile_equal": prof32 == prof64, "logF_fp64": lf64,
+                     "overlap": ov})
+        ref.close()
+    mps.close()
+    d_logF = abs(logF_packed - logF_sum)
+    line = {"metric": "cluster updates/s, packed circuits (cfg5) vs each circuit's FP64-mode run",
+            "value": counts["updates"] / wall, "unit": "cluster updates/s", "higher_is_better": True,
+            "n_gpus": 1, "dtype": "c64", "data": "synthetic (seeded circuits from |0...0>)",
+            "config": {"workload": f"cfg5: {args.circuits} Clifford+T circuits, n ~ U[50, 300] "
+                                   f"(total {sum(x[0] for x in spec)} qubits), layers ~ U[40, 100], "
+                                   "T density ~ U[5%, 25%], chi_max=1024, cutoff 1e-8, k_max=4, packed per step",
+                       "timing": "wall clock of the whole packed simulation, host partition included"},
+            "updates": counts["updates"], "iterations": counts["iterations"], "wall_s": wall,
+            "fp64_mode_alone_s": t64, "fp64_updates_per_s": counts["updates"] / t64,
+            "agreement": {"circuits": len(rows),
+                          "chi_profiles_equal": int(sum(r["chi_profile_equal"] for r in rows)),
+                          "min_overlap": min(r["overlap"] for r in rows),
+                          "abs_dlogF_total": d_logF,
+                          "max_chi": max(r["max_chi"] for r in rows),
+                          "truncated_circuits": int(sum(r["logF_fp64"] < -1e-6 for r in rows))},
+            "circuits": rows}
+    print(json.dumps(line))
+
+
+def run_latency(args):
+    """Where latency dominates: cfg1 (n=12, exact, FP64), cfg3's gate
+    statistics at n=40 (Clifford, chi_max 512, cutoff 1e-12) and cfg2's at
+    n=100 over 20 layers, each from |0...0> through the whole circuit.  Per
+    configuration: the wall time of the step calls, and the summed device time
+    of the library's kernels in a second, identical run with per-launch CUDA
+    events.  Their ratio is the fraction of the step the GPU is busy; the rest
+    is host work, launch gaps and the per-level reads, the most that capturing
+    a whole step into one graph could remove."""
+    import ctypes as C
+
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import synth
+
+    def run(w, base, profile):
+        n, chi = w.n_qubits, w.chi_max
+        q_max = w.k_max + 2 * int(math.log2(chi))
+        prec = P.FP64 if w.precision == "fp64" else P.FP32
+        cfg = P.make_config(n, chi, w.cutoff, q_max, 0, w.k_max, prec)
+        c = w.circuit(0, base)
+        circ = P.Circuit(n, c.gates, c.params)
+        stream = torch.cuda.Stream()
+        mps = P.MPS(cfg, stream.cuda_stream)
+        if profile:
+            P._check(P.lib.ctebd_profile(mps._h, 1), "ctebd_profile")
+        start, steps, upd, t_step = 0, 0, 0, 0.0
+        torch.cuda.synchronize()
+        while start < circ.n_layers:
+            cl, stop = P.cluster_partition(circ.gates, circ.n_gates, start, mps.bond_dims(), cfg)
+            mps.apply_singletons(circ.gates, circ.n_gates, cl, start, stop)
+            if cl:
+                Us = [P.cluster_unitary(circ.gates, circ.n_gates, x) for x in cl]
+                t0 = time.perf_counter()
+                mps.step(cl, Us)
+                t_step += time.perf_counter() - t0
+                steps += 1
+                upd += len(cl)
+            start = stop
+        out = {"steps": steps, "updates": upd, "step_wall_s": t_step, "max_chi": int(max(mps.bond_dims())),
+               "logF": float(math.log(mps.fidelity()))}
+        if profile:
+            rows = np.zeros(5 * 32)
+            nk = C.c_int(0)
+            P._check(P.lib.ctebd_profile_read(mps._h, rows.ctypes.data_as(C.POINTER(C.c_double)), 32,
+                                              C.byref(nk)), "ctebd_profile_read")
+            out["kernel_ms"] = float(sum(rows[5 * k + 1] for k in range(nk.value)))
+            out["launches"] = int(sum(rows[5 * k] for k in range(nk.value)))
+        mps.close()
+        return out
+
+    res = {}
+    for name, base, w in (("cfg1: n=12, 10 layers, exact, FP64", 1, synth.WORKLOADS[1]),
+                          ("cfg3 statistics: n=40, 100 layers, Clifford, chi_max 512", 3, synth.reduced(3, 40, 100)),
+                          ("cfg2 statistics: n=100, 20 layers", 2, synth.reduced(2, 100, 20))):
+        run(w, base, False)   # warm-up
+        plain = run(w, base, False)
+        prof = run(w, base, True)
+        res[name] = {"updates_per_s": plain["updates"] / plain["step_wall_s"], "steps": plain["steps"],
+                     "step_ms": 1e3 * plain["step_wall_s"] / max(plain["steps"], 1),
+                     "kernel_ms_per_step": prof["kernel_ms"] / max(prof["steps"], 1),
+                     "launches_per_step": prof["launches"] / max(prof["steps"], 1),
+                     "gpu_busy_frac": prof["kernel_ms"] / 1e3 / plain["step_wall_s"],
+                     "max_chi": plain["max_chi"]}
+    print(json.dumps({"metric": "GPU-busy fraction of the step on latency-bound configurations",
+                      "unit": "fraction", "n_gpus": 1, "data": "synthetic (seeded circuits from |0...0>)",
+                      "configs": res}))
 
 
 def aggregate(dev_s: float, wall_s: float, units: int, device=None):
@@ -495,6 +651,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     device = f"cuda:{local_rank}"
     stream = torch.cuda.Stream(device=device)
+    if args.tensor_cores is not None:
+        P.set_tensor_cores(args.tensor_cores)
     w = synth.WORKLOADS[4]
     n, chi, kmax = args.n, args.chi, args.kmax
     q_max = kmax + 2 * int(math.log2(chi))
@@ -799,12 +957,16 @@ def main():
                     help="largest cluster (Q_max = kmax + 2 log2 chi); 6 lets k = 3..6 clusters form")
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "compare", "apply-traffic"],
+    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "cfg5", "compare", "apply-traffic", "latency"],
                     help="cfg4: the headline (saturated chi=1024, full split); cfg2, sketch-cfg4: full vs "
                          "sketched split (cfg2, and cfg4's growing phase); "
-                         "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations")
+                         "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations; "
+                         "apply-traffic: small case for the round update's DRAM traffic; latency: GPU-busy "
+                         "fraction of the step on small configurations; cfg5: packed circuits, each "
+                         "checked against its FP64-mode run")
+    ap.add_argument("--circuits", type=int, default=64, help="cfg5: number of packed circuits")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
-                    help="apply-traffic mode: tensor-core policy (0 never, 1 size policy, 2 always, "
+                    help="tensor-core policy (default 1, the size policy; 0 never; 2 always, "
                          "including the Jacobi round updates)")
     ap.add_argument("--layers", type=int, default=0,
                     help="cfg2 / sketch-cfg4: circuit depth (default: 50 / 30)")
@@ -816,6 +978,12 @@ def main():
         return
     if args.workload == "compare":
         run_compare(args)
+        return
+    if args.workload == "latency":
+        run_latency(args)
+        return
+    if args.workload == "cfg5":
+        run_cfg5(args)
         return
     if args.workload == "apply-traffic":
         run_apply_traffic(args)
@@ -830,6 +998,9 @@ def main():
                 "synthetic saturated state (all interior bonds at chi_max)")
     config = {"workload": workload, "precision": "complex64 contractions, fp64 spectra/weights",
               "l2": "inputs larger than L2 (theta/Gram per step >> 129 MB)", "replicas": world}
+    if args.tensor_cores is not None:
+        config["tensor_cores"] = {0: "never", 1: "size policy", 2: "always, Jacobi round updates included"}[
+            args.tensor_cores]
 
     if args.impl == "reference":
         if rank != 0:
