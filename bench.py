@@ -527,12 +527,11 @@ def run_cfg5(args):
         t64 += time.perf_counter() - a
         lf64 = float(math.log(ref.fidelity()))
         logF_sum += lf64
-        prof64 = list(ref.bond_dims())
-        prof32 = list(chis[off:off + n + 1])
+        prof64 = [int(x) for x in ref.bond_dims()]
+        prof32 = [int(x) for x in chis[off:off + n + 1]]
         a_sites = [torch.as_tensor(mps.site(off + q)).to(torch.complex128) for q in range(n)]
         b_sites = [torch.as_tensor(ref.site(q)).to(torch.complex128) for q in range(n)]
         ov = mps_overlap(torch, a_sites, b_sites)
-        # the circuit's own fidelity product inside the packed run: its splits' f
         rows.append({"n": n, "max_chi": max(prof64), "chi_profile_equal": prof32 == prof64, "logF_fp64": lf64,
                      "overlap": ov})
         ref.close()

@@ -620,8 +620,14 @@ static void work_sizes(const ctebd_mps* m, Work& w) {
     big = std::max(big, rows * (size_t)m->chi[q0 + j]);
     rows *= 2;
   }
-  // split level shapes: n <= 2 * min(chi_max, bound)
-  const size_t nmax = std::min<size_t>(2 * (size_t)std::max(m->cfg.chi_max, w.chiR), (size_t)1 << 30);
+  // split level shapes: the Gram of the split at bond q0 + j is n x n with
+  // n = 2 r, r the rank kept at bond q0 + j + 1 (chi_R for the first split,
+  // j = k - 1), and r <= min(chi_max, chi_L 2^(j+1), chi_R 2^(k-j-1)) (the
+  // ranks of the matrices split there)
+  size_t nmax = 2 * (size_t)w.chiR;
+  for (int j = 1; j < k - 1; j++)
+    nmax = std::max(nmax, 2 * std::min({(size_t)m->cfg.chi_max, (size_t)w.chiL << (j + 1),
+                                        (size_t)w.chiR << (k - j - 1)}));
   const int JB = eig_block(m->fp64);
   const size_t npad = round_up(nmax, 2 * JB);
   w.bufElems = big;

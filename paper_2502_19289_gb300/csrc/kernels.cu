@@ -191,9 +191,12 @@ __device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R flo
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ probs, int round) {
+__global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict__ probs, int round) {
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, NBLK = JB * (JB + 1) / 2;
+  constexpr int NB_T = (NBLK + 255) / 256, QROWS = D * JB / 256;   // per thread: A blocks, Q rows
+  constexpr unsigned PMASK = JB == 32 ? 0xffffffffu : ((1u << JB) - 1u);   // lanes of the parameter phase
+  static_assert(256 % JB == 0 && (D * JB) % 256 == 0, "inner kernel: 256 threads");
   const EigProb P = probs[blockIdx.y];
   if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2) return;
   extern __shared__ unsigned char smraw[];
@@ -257,8 +260,9 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
           }
         }
         tu[threadIdx.x] = s / ((R)1 + c); sn[threadIdx.x] = s; ph[threadIdx.x] = e;
-        if (!skip) atomicAdd(&nrot, 1);
-        if (sig) atomicAdd(&nsig, 1);
+        // rotation counters: one shared-memory update per round, by lane 0
+        const unsigned mr = __ballot_sync(PMASK, !skip), ms = __ballot_sync(PMASK, sig);
+        if (threadIdx.x == 0) { nrot += __popc(mr); nsig += __popc(ms); }
       }
       __syncthreads();
       // A <- R^H A R and Q <- Q R, every rotation in Rutishauser's form
@@ -268,17 +272,41 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
       // round act on disjoint pairs, so the 2 x 2 block of A on pairs (a, b)
       // becomes R_a^H B R_b by itself: one thread per block with a <= b, the
       // block below the diagonal is its conjugate transpose (A stays Hermitian).
-      for (int e = threadIdx.x; e < NBLK; e += blockDim.x) {
-        const int a = blk[e] & 0xff, b = blk[e] >> 8;
+      // Every element a thread touches in a round is its own, so all of its
+      // loads (A blocks, Q pairs) are issued before any arithmetic or store.
+      int ia[NB_T], ib[NB_T];
+      CT x00[NB_T], x10[NB_T], x01[NB_T], x11[NB_T];
+#pragma unroll
+      for (int u = 0; u < NB_T; u++) {
+        const int e = threadIdx.x + 256 * u;
+        const int bb = e < NBLK ? blk[e] : 0;
+        ia[u] = bb & 0xff;
+        ib[u] = bb >> 8;
+        const int pa = pp[ia[u]], qa = pq[ia[u]], pb = pp[ib[u]], qb = pq[ib[u]];
+        x00[u] = A[pa * LD + pb]; x10[u] = A[qa * LD + pb];
+        x01[u] = A[pa * LD + qb]; x11[u] = A[qa * LD + qb];
+      }
+      const int kq = threadIdx.x % JB, row0 = threadIdx.x / JB;   // Q: one rotation per thread
+      const int pq_p = pp[kq], pq_q = pq[kq];
+      CT xq[QROWS], yq[QROWS];
+#pragma unroll
+      for (int j = 0; j < QROWS; j++) {
+        const int row = row0 + j * (256 / JB);
+        xq[j] = Q[row * LD + pq_p];
+        yq[j] = Q[row * LD + pq_q];
+      }
+#pragma unroll
+      for (int u = 0; u < NB_T; u++) {
+        if (threadIdx.x + 256 * u >= NBLK) continue;
+        const int a = ia[u], b = ib[u];
         const int pa = pp[a], qa = pq[a], pb = pp[b], qb = pq[b];
-        const CT x00 = A[pa * LD + pb], x10 = A[qa * LD + pb];
         const R tb = tu[b], sb = sn[b];
         const CT fb = ph[b];
-        const CT y0 = cmul(A[pa * LD + qb], fb), y1 = cmul(A[qa * LD + qb], fb);
-        const CT n00 = cmk<CT>(x00.x - sb * (y0.x + tb * x00.x), x00.y - sb * (y0.y + tb * x00.y));
-        const CT n01 = cmk<CT>(y0.x + sb * (x00.x - tb * y0.x), y0.y + sb * (x00.y - tb * y0.y));
-        const CT n10 = cmk<CT>(x10.x - sb * (y1.x + tb * x10.x), x10.y - sb * (y1.y + tb * x10.y));
-        const CT n11 = cmk<CT>(y1.x + sb * (x10.x - tb * y1.x), y1.y + sb * (x10.y - tb * y1.y));
+        const CT y0 = cmul(x01[u], fb), y1 = cmul(x11[u], fb);
+        const CT n00 = cmk<CT>(x00[u].x - sb * (y0.x + tb * x00[u].x), x00[u].y - sb * (y0.y + tb * x00[u].y));
+        const CT n01 = cmk<CT>(y0.x + sb * (x00[u].x - tb * y0.x), y0.y + sb * (x00[u].y - tb * y0.y));
+        const CT n10 = cmk<CT>(x10[u].x - sb * (y1.x + tb * x10[u].x), x10[u].y - sb * (y1.y + tb * x10[u].y));
+        const CT n11 = cmk<CT>(y1.x + sb * (x10[u].x - tb * y1.x), y1.y + sb * (x10[u].y - tb * y1.y));
         const R ta = tu[a], sa = sn[a];
         const CT fa = cconj(ph[a]);
         const CT z0 = cmul(n10, fa), z1 = cmul(n11, fa);
@@ -293,13 +321,16 @@ __global__ void __launch_bounds__(256) k_eig_inner(const EigProb* __restrict__ p
           A[pb * LD + qa] = cconj(m10); A[qb * LD + qa] = cconj(m11);
         }
       }
-      for (int e = threadIdx.x; e < D * JB; e += blockDim.x) {   // columns of Q
-        const int row = e / JB, k = e % JB;
-        const int p = pp[k], q = pq[k];
-        const R t = tu[k], s = sn[k];
-        const CT x = Q[row * LD + p], y = cmul(Q[row * LD + q], ph[k]);
-        Q[row * LD + p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
-        Q[row * LD + q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
+      {
+        const R t = tu[kq], s = sn[kq];
+        const CT f = ph[kq];
+#pragma unroll
+        for (int j = 0; j < QROWS; j++) {
+          const int row = row0 + j * (256 / JB);
+          const CT x = xq[j], y = cmul(yq[j], f);
+          Q[row * LD + pq_p] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
+          Q[row * LD + pq_q] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
+        }
       }
       __syncthreads();
     }
