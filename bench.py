@@ -666,6 +666,7 @@ def run_ours(args, rank, world, local_rank):
     totals = {"updates": 0, "dev_ms": 0.0, "wall_s": 0.0, "h2d": 0, "d2h": 0, "flops": 0.0,
               "f_merge": 0.0, "f_u": 0.0, "f_split": 0.0}
     step_f = []
+    sweeps = []   # Jacobi sweeps (pass 1, pass 2) of every split of the timed steps
 
     def one_step(timed):
         nonlocal start
@@ -690,7 +691,10 @@ def run_ours(args, rank, world, local_rank):
             totals["wall_s"] += t1 - t0
             totals["h2d"] += sum(16 * U.size for U in Us)
             totals["d2h"] += 8 * len(f) + 4 * len(chi_after)
-            fm, fu, fs = method_flops(clusters, chi_now, mps.split_log())
+            log = mps.split_log()
+            fm, fu, fs = method_flops(clusters, chi_now, log)
+            if len(log):
+                sweeps.append(log[:, 12:14])
             totals["f_merge"] += fm
             totals["f_u"] += fu
             totals["f_split"] += fs
@@ -724,6 +728,12 @@ def run_ours(args, rank, world, local_rank):
     res["counts"] = counts
     res["clocks"] = clk.summary()
     res["steps_detail"] = step_f
+    sw = np.concatenate(sweeps) if sweeps else np.zeros((0, 2))
+    res["jacobi_sweeps"] = {"splits": int(len(sw)), "cap": P.max_sweeps(),
+                            "pass1_mean": float(sw[:, 0].mean()) if len(sw) else 0.0,
+                            "pass1_max": int(sw[:, 0].max()) if len(sw) else 0,
+                            "pass2_mean": float(sw[:, 1].mean()) if len(sw) else 0.0,
+                            "pass2_max": int(sw[:, 1].max()) if len(sw) else 0}
     res["peaks"] = measure_compute_peaks(P, torch, device)
 
     # plain FP64 comparator on a sample of the next iteration's clusters
@@ -1119,6 +1129,7 @@ def main():
         "clocks": clocks,
         "updates": units,
         "steps_detail": res["steps_detail"],
+        "jacobi_sweeps": res["jacobi_sweeps"],
     }
     if "plain" in res and "error" in res["plain"]:
         line["plain_fp64"] = res["plain"]

@@ -293,18 +293,23 @@ int ctebd_set_tensor_cores(int mode);
 
 /* Eigen-solve sweep loop on the device (not in the paper): with per-launch
    profiling off, each batched eigen-solve runs as one CUDA graph whose WHILE
-   node repeats a sweep until every problem has converged (or 30 sweeps), with
+   node repeats a sweep until every problem has converged (or the sweep cap), with
    no host round trip per sweep.  on = 1 (default) uses it, 0 launches every
    round from the host.  Process-wide; results are the same either way.
    Returns CTEBD_ERR_ARG for other values. */
 int ctebd_set_sweep_graphs(int on);
 
 /* Sweep cap of the Jacobi eigen-solves of the split (not in the paper; the
-   solver of this implementation), process-wide, 1..1000 (default 30).  A
-   solve whose problems still make significant rotations after n sweeps makes
-   step / truncate_split / split2_noalloc return CTEBD_ERR_NUMERIC (the state's
-   sites of that iteration are then undefined).  Errors: ARG. */
+   solver of this implementation), process-wide, 1..1000 (default 60: the
+   first pass takes about 10 sweeps at width 2048, the refinement pass up to
+   about 20 on steep spectra).  A solve whose problems still make significant
+   rotations after n sweeps makes step / truncate_split / split2_noalloc return
+   CTEBD_ERR_NUMERIC (the state's sites of that iteration are then
+   undefined).  Errors: ARG. */
 int ctebd_set_max_sweeps(int n);
+
+/* The current sweep cap. */
+int ctebd_max_sweeps(void);
 
 /* Per-kernel-class accounting.  ctebd_profile(mps, 1) clears the counters
    and starts CUDA-event timing of every launch on the handle's stream (0

@@ -85,6 +85,7 @@ def _load():
         "ctebd_set_tensor_cores": [I],
         "ctebd_set_sweep_graphs": [I],
         "ctebd_set_max_sweeps": [I],
+        "ctebd_max_sweeps": [],
         "virtual_mps_bonds": [C.POINTER(Gate), I, I, I, I, C.POINTER(I), I, C.POINTER(I), C.POINTER(I)],
         "adaptive_grouping": [C.POINTER(I), I, I, D, C.POINTER(I), I, C.POINTER(I)],
         "ctebd_measure_fma": [I, C.POINTER(D), C.POINTER(D), C.POINTER(I)],
@@ -210,9 +211,14 @@ def set_sweep_graphs(on: bool):
 
 
 def set_max_sweeps(n: int):
-    """Sweep cap of the Jacobi eigen-solves (default 30); a solve still rotating at
+    """Sweep cap of the Jacobi eigen-solves (default 60); a solve still rotating at
     the cap makes the split fail with CTEBD_ERR_NUMERIC; process-wide."""
     _check(_lib.ctebd_set_max_sweeps(int(n)), "ctebd_set_max_sweeps")
+
+
+def max_sweeps() -> int:
+    """The current sweep cap of the Jacobi eigen-solves."""
+    return int(_lib.ctebd_max_sweeps())
 
 
 def measure_fma(repeats: int = 5):

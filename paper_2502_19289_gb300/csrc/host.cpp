@@ -400,6 +400,8 @@ struct ctebd_mps {
   int* tc_err = nullptr;           // tensor-core completion-wait timeout flag (device)
   double* eig_scr = nullptr;       // eigen-solve counters and pair flags (high-water)
   size_t eig_scr_cap = 0;          // in doubles
+  unsigned char* pack_scr = nullptr;   // packed tensor-core GEMM operands (high-water)
+  size_t pack_cap = 0;                 // in bytes
   cudaStream_t side = nullptr;     // second branch of the device-side sweep graphs
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* arena = nullptr;
@@ -496,6 +498,7 @@ extern "C" int mps_destroy(ctebd_mps* m) {
   if (m->mlp) cudaFree(m->mlp);
   if (m->tc_err) cudaFree(m->tc_err);
   if (m->eig_scr) cudaFree(m->eig_scr);
+  if (m->pack_scr) cudaFree(m->pack_scr);
   if (m->h_res) cudaFreeHost(m->h_res);
   m->stage.release();
   m->prof.release();
@@ -536,6 +539,22 @@ static int ensure_eig_scratch(ctebd_mps* m, size_t n) {
   return CTEBD_OK;
 }
 
+// grow the packed-operand scratch to at least n bytes (synchronises only when it grows)
+static int ensure_pack_scratch(ctebd_mps* m, size_t n) {
+  if (n <= m->pack_cap) return CTEBD_OK;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (m->pack_scr) CUDA_TRY(cudaFree(m->pack_scr));
+  m->pack_scr = nullptr;
+  m->pack_cap = 0;
+  const size_t want = n + n / 4;
+  if (cudaMalloc(&m->pack_scr, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CTEBD_ERR_OOM, "packed GEMM operands of " + std::to_string(want >> 20) + " MiB");
+  }
+  m->pack_cap = want;
+  return CTEBD_OK;
+}
+
 // the device flag that a tensor-core kernel sets when a bounded wait expires
 static int ensure_tc_err(ctebd_mps* m) {
   if (m->tc_err) return CTEBD_OK;
@@ -543,6 +562,8 @@ static int ensure_tc_err(ctebd_mps* m) {
   CUDA_TRY(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
   return CTEBD_OK;
 }
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static double gemm_flops(const GemmProb& g) { return 8.0 * g.M * g.N * (double)g.K * g.batch; }
 
@@ -567,20 +588,53 @@ static int launch_gemm_group(ctebd_mps* m, const std::vector<GemmProb>& probs, i
     fl += gemm_flops(g);
     by += gemm_bytes(g, m->esz);
   }
+  if (tc) {
+    // tensor cores: the operands of a run of problems are packed into the
+    // scratch (at most kPackGroup bytes per run, or one problem), then
+    // multiplied; consecutive runs reuse the scratch in stream order
+    constexpr size_t kPackGroup = (size_t)8 << 30;
+    TRY(ensure_tc_err(m));
+    ProfScope ps(m->prof, m->stream, kind, fl, by);
+    for (size_t i0 = 0; i0 < probs.size();) {
+      size_t bytes = 0, i1 = i0;
+      while (i1 < probs.size()) {
+        const size_t b = round_up(tc_packed_bytes(probs[i1]), 256);
+        if (i1 > i0 && bytes + b > kPackGroup) break;
+        bytes += b;
+        i1++;
+      }
+      TRY(ensure_pack_scratch(m, bytes));
+      const int np = (int)(i1 - i0);
+      std::vector<PackedProb> pp(np);
+      std::vector<long long> poff(np + 1, 0), toff(np + 1, 0);
+      unsigned char* p = m->pack_scr;
+      for (int i = 0; i < np; i++) {
+        PackedProb& q = pp[i];
+        q.g = probs[i0 + i];
+        tc_packed_shape(q.g, q.tilesM, q.tilesN, q.chunks);
+        q.pa = reinterpret_cast<float*>(p);
+        q.pb = reinterpret_cast<float*>(p + tc_packed_a_bytes(q.g));
+        p += round_up(tc_packed_bytes(q.g), 256);
+        poff[i + 1] = poff[i] + tc_packed_pack_blocks(q.g);
+        toff[i + 1] = toff[i] + tc_packed_tiles(q.g);
+      }
+      const PackedProb* dpp;
+      const long long *dpo, *dto;
+      TRY(m->stage.push(pp.data(), pp.size(), &dpp));
+      TRY(m->stage.push(poff.data(), poff.size(), &dpo));
+      TRY(m->stage.push(toff.data(), toff.size(), &dto));
+      m->prof.tc[kind] += 1;
+      CUDA_TRY(launch_tc_packed(dpp, dpo, dto, np, poff.back(), toff.back(), m->tc_err, m->stream));
+      i0 = i1;
+    }
+    return CTEBD_OK;
+  }
   std::vector<long long> off(probs.size() + 1, 0);
-  for (size_t i = 0; i < probs.size(); i++)
-    off[i + 1] = off[i] + (tc ? tc_gemm_tiles(probs[i]) : gemm_tiles(probs[i], m->fp64));
+  for (size_t i = 0; i < probs.size(); i++) off[i + 1] = off[i] + gemm_tiles(probs[i], m->fp64);
   const GemmProb* dp;
   const long long* doff;
   TRY(m->stage.push(probs.data(), probs.size(), &dp));
   TRY(m->stage.push(off.data(), off.size(), &doff));
-  if (tc) {
-    TRY(ensure_tc_err(m));
-    ProfScope ps(m->prof, m->stream, kind, fl, by);
-    m->prof.tc[kind] += 1;
-    CUDA_TRY(launch_tc_gemm(dp, doff, (int)probs.size(), off.back(), m->tc_err, m->stream));
-    return CTEBD_OK;
-  }
   ProfScope ps(m->prof, m->stream, kind, fl, by);
   cudaError_t e = m->fp64 ? launch_gemm<double>(dp, doff, (int)probs.size(), off.back(), m->stream)
                           : launch_gemm<float>(dp, doff, (int)probs.size(), off.back(), m->stream);
@@ -608,8 +662,6 @@ static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind)
   TRY(launch_gemm_group(m, tc, kind, true));
   return launch_gemm_group(m, simt, kind, false);
 }
-
-static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // sizes of one cluster's work buffers
 static void work_sizes(const ctebd_mps* m, Work& w) {
@@ -829,7 +881,7 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // off (ctebd_set_sweep_graphs; process-wide).
 // ---------------------------------------------------------------------------
 static int g_sweep_graphs = 1;
-static int g_max_sweeps = 30;
+static int g_max_sweeps = 60;
 
 namespace ctebd {
 int max_jacobi_sweeps() { return g_max_sweeps; }
@@ -840,6 +892,8 @@ extern "C" int ctebd_set_max_sweeps(int n) {
   g_max_sweeps = n;
   return CTEBD_OK;
 }
+
+extern "C" int ctebd_max_sweeps(void) { return g_max_sweeps; }
 
 extern "C" int ctebd_set_sweep_graphs(int on) {
   if (on < 0 || on > 1) return fail(CTEBD_ERR_ARG, "ctebd_set_sweep_graphs: 0 or 1");
@@ -2154,19 +2208,34 @@ extern "C" int mlp_adam(float* params, const float* grad, float* m1, float* m2, 
 }
 
 // C (M x N) = A (M x K) B (K x N), complex64 row-major device buffers, on the
-// tensor cores (3xTF32); M % 128 == 0, N % 64 == 0, K % 32 == 0.  Used to
-// validate the tile engine against a reference product.
+// tensor cores (3xTF32, packed operands), any sizes.  Used to validate the
+// tile engine against a reference product.
 extern "C" int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* stream) {
-  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 64 || K % 16)
-    return fail(CTEBD_ERR_ARG, "tc_cgemm: M % 128, N % 64, K % 16 must be 0");
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0) return fail(CTEBD_ERR_ARG, "tc_cgemm: bad args");
   cudaStream_t s = (cudaStream_t)stream;
-  int* err = nullptr;
-  CUDA_TRY(cudaMallocAsync(&err, sizeof(int), s));
+  PackedProb q{};
+  GemmProb& g = q.g;
+  g.M = M; g.N = N; g.K = K; g.batch = 1;
+  g.A = A; g.lda = K; g.B = B; g.ldb = N; g.C = C; g.ldc = N; g.alpha = 1.0;
+  tc_packed_shape(g, q.tilesM, q.tilesN, q.chunks);
+  const size_t pbytes = tc_packed_bytes(g);
+  const long long off[4] = {0, tc_packed_pack_blocks(g), 0, tc_packed_tiles(g)};
+  unsigned char* buf = nullptr;
+  const size_t head = 1024;   // err flag, descriptor, offsets
+  CUDA_TRY(cudaMallocAsync((void**)&buf, head + pbytes, s));
+  q.pa = reinterpret_cast<float*>(buf + head);
+  q.pb = reinterpret_cast<float*>(buf + head + tc_packed_a_bytes(g));
+  int* err = reinterpret_cast<int*>(buf);
+  static_assert(sizeof(PackedProb) <= 512, "tc_cgemm: descriptor slot");
+  PackedProb* dq = reinterpret_cast<PackedProb*>(buf + 256);
+  long long* doff = reinterpret_cast<long long*>(buf + 768);
   CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  CUDA_TRY(launch_tc_plain(A, B, C, M, K, N, err, s));
+  CUDA_TRY(cudaMemcpyAsync(dq, &q, sizeof(q), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(doff, off, sizeof(off), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_tc_packed(dq, doff, doff + 2, 1, off[1], off[3], err, s));
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaFreeAsync(err, s));
+  CUDA_TRY(cudaFreeAsync(buf, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (h) return fail(CTEBD_ERR_TIMEOUT, "tc_cgemm: tensor-core completion wait timed out");
   return CTEBD_OK;

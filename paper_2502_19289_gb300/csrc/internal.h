@@ -211,6 +211,27 @@ long long tc_gemm_tiles(const GemmProb& p);
 cudaError_t launch_tc_gemm(const GemmProb* d_probs, const long long* d_tile_off, int n_probs,
                            long long total_tiles, int* err, cudaStream_t s);
 
+// tensor-core complex GEMM on operands packed once per launch (tc_packed.cu):
+// op(A) as 32 KB blocks per (batch, 128-row tile, 16-complex K chunk), op(B)
+// as 16 KB blocks per (batch, 64-column tile, chunk), each block four TF32
+// planes (Re hi / lo, Im hi / lo); pa and pb point into a scratch buffer of
+// tc_packed_bytes(g) (A blocks first, tc_packed_a_bytes(g) of them)
+struct PackedProb {
+  GemmProb g;
+  float* pa;
+  float* pb;
+  int tilesM, tilesN, chunks;
+};
+void tc_packed_shape(const GemmProb& g, int& tilesM, int& tilesN, int& chunks);
+size_t tc_packed_bytes(const GemmProb& g);
+size_t tc_packed_a_bytes(const GemmProb& g);
+long long tc_packed_pack_blocks(const GemmProb& g);
+long long tc_packed_tiles(const GemmProb& g);
+// pack (one block per operand block, prefix offsets d_pack_off) then product
+// (one CTA per output tile, prefix offsets d_tile_off)
+cudaError_t launch_tc_packed(const PackedProb* d_probs, const long long* d_pack_off, const long long* d_tile_off,
+                             int n_probs, long long pack_blocks, long long tiles, int* err, cudaStream_t s);
+
 // message returned by ctebd_last_error() in the calling thread
 void set_last_error(const std::string& msg);
 

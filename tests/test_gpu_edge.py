@@ -60,6 +60,7 @@ def test_sweep_cap_reports_numeric_error(graphs):
     chis, sites, lams = synth.random_right_canonical(12, 64, seed=77)
     U = np.linalg.qr(np.random.default_rng(77).standard_normal((4, 4)))[0].astype(np.complex128)
     cfg = P.make_config(12, 64, 1e-8, 2 + 12 + 2, 0, 2, P.FP32)
+    cap = P.max_sweeps()
     try:
         P.set_sweep_graphs(graphs)
         P.set_max_sweeps(1)
@@ -68,7 +69,7 @@ def test_sweep_cap_reports_numeric_error(graphs):
         with pytest.raises(P.CtebdError, match="still rotating after 1 sweeps"):
             mps.step([P.Cluster(5, 2, 0, 0)], [U])
     finally:
-        P.set_max_sweeps(30)
+        P.set_max_sweeps(cap)
         P.set_sweep_graphs(True)
     mps = P.MPS(cfg)
     mps.load(chis, sites, lams)

@@ -1,5 +1,5 @@
-"""GPU: the tcgen05 tile engine (3xTF32 complex products) against a complex128
-reference product."""
+"""GPU: the tcgen05 tile engine (3xTF32 complex products on packed operands)
+against a complex128 reference product, at tile multiples and ragged sizes."""
 import numpy as np
 import pytest
 
@@ -8,7 +8,8 @@ from gpu_helpers import lib
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("M,K,N", [(128, 32, 64), (256, 96, 128), (384, 64, 192), (256, 2048, 128)])
+@pytest.mark.parametrize("M,K,N", [(128, 32, 64), (256, 96, 128), (384, 64, 192), (256, 2048, 128),
+                                   (200, 37, 50), (1000, 301, 130), (1, 5, 3), (129, 16, 65)])
 def test_tc_cgemm_matches_reference(M, K, N):
     torch = pytest.importorskip("torch")
     P = lib()
