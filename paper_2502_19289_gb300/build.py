@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libctebd.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host.cpp", "kernels.cu", "sketch.cu", "mlp.cu", "noalloc.cu", "tc_gemm.cu", "eig_tc.cu", "tc_packed.cu"]
+SOURCES = ["host.cpp", "kernels.cu", "sketch.cu", "mlp.cu", "noalloc.cu", "eig_tc.cu", "tc_packed.cu"]
 
 
 def _nvcc() -> str:

@@ -572,14 +572,6 @@ static double gemm_bytes(const GemmProb& g, size_t esz) {
           (double)g.M * g.N * g.batch) * esz;
 }
 
-// the tensor-core kernel copies operand chunks with 16-byte cp.async when
-// every granule it copies starts on a 16-byte boundary
-static int tc_async_ok(const GemmProb& g) {
-  const bool a_al = ((uintptr_t)g.A & 15) == 0 && g.lda % 2 == 0 && (g.batch == 1 || g.sA % 2 == 0);
-  const bool b_al = ((uintptr_t)g.B & 15) == 0 && g.ldb % 2 == 0 && (g.batch == 1 || g.sB % 2 == 0);
-  return a_al && b_al ? 1 : 0;
-}
-
 // one grouped launch of probs on the tensor cores (tc) or the SIMT kernel
 static int launch_gemm_group(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind, bool tc) {
   if (probs.empty()) return CTEBD_OK;
@@ -648,17 +640,12 @@ static int launch_gemm_group(ctebd_mps* m, const std::vector<GemmProb>& probs, i
 static int run_gemms(ctebd_mps* m, const std::vector<GemmProb>& probs, int kind) {
   if (probs.empty()) return CTEBD_OK;
   if (m->fp64 || g_tc_mode == 0) return launch_gemm_group(m, probs, kind, false);
-  if (g_tc_mode == 2) {
-    std::vector<GemmProb> all(probs);
-    for (GemmProb& g : all) g.async_ok = tc_async_ok(g);
-    return launch_gemm_group(m, all, kind, true);
-  }
+  if (g_tc_mode == 2) return launch_gemm_group(m, probs, kind, true);
   double fl = 0;
   for (const GemmProb& g : probs) fl += gemm_flops(g);
   if (fl < 2e9) return launch_gemm_group(m, probs, kind, false);
   std::vector<GemmProb> tc, simt;
   for (const GemmProb& g : probs) (g.M >= 64 ? tc : simt).push_back(g);
-  for (GemmProb& g : tc) g.async_ok = tc_async_ok(g);
   TRY(launch_gemm_group(m, tc, kind, true));
   return launch_gemm_group(m, simt, kind, false);
 }

@@ -25,8 +25,6 @@ struct GemmProb {
   int kw_shift;
   double alpha;
   int kw_pow;   // 1: multiply by kw; otherwise by kw^2
-  int async_ok; // tensor-core path: A and B 16-byte aligned, even leading dimensions and
-                // batch strides -- operand chunks are then copied with cp.async
 };
 
 // One Hermitian eigenproblem of the batched block-Jacobi solver.  G and V are
@@ -204,12 +202,6 @@ cudaError_t launch_mlp_loss_grad(const float* params, const float* X, const int*
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int t, cudaStream_t s);
 cudaError_t launch_entropy(const double* const* d_lams, const int* d_chi, int nb, double* d_out, cudaStream_t s);
 
-// tensor-core (tcgen05, 3xTF32) complex tile products
-cudaError_t launch_tc_plain(const void* A, const void* B, void* C, int M, int K, int N, int* err,
-                            cudaStream_t s);
-long long tc_gemm_tiles(const GemmProb& p);
-cudaError_t launch_tc_gemm(const GemmProb* d_probs, const long long* d_tile_off, int n_probs,
-                           long long total_tiles, int* err, cudaStream_t s);
 
 // tensor-core complex GEMM on operands packed once per launch (tc_packed.cu):
 // op(A) as 32 KB blocks per (batch, 128-row tile, 16-complex K chunk), op(B)
