@@ -69,7 +69,9 @@ constexpr int KC = 16;                     // complex K per chunk
 constexpr int NCH = 4;                     // chunks: K = 64 complex
 constexpr int NT = 512;                    // threads per CTA: 8 producer + 8 epilogue warps
 constexpr int GT = 256;                    // threads per group
-constexpr uint32_t LBO = 128, SBO = 1024;  // core matrices along K / along rows
+#if !ETC_SWIZZLE
+constexpr uint32_t LBO = 128, SBO = 1024;  // core matrices along K / along rows (no-swizzle layout)
+#endif
 constexpr int OPB = 16 * 1024;             // one 128 x 32 real operand piece
 constexpr int STB = 4 * OPB;               // one operand stage: A hi, A lo, B hi, B lo
 constexpr int RAWA = 16 * 1024;            // raw A chunk (128 x 16 complex)

@@ -941,7 +941,7 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector
     }
     if (le == cudaSuccess) le = chain(dep, na0, nb0, m->stream);
     if (le == cudaSuccess && na1 > 0) le = cudaStreamWaitEvent(m->stream, m->join_ev, 0);
-    if (le == cudaSuccess) le = launch_sweep_end(dep, na, d_cum, d_cum + 3 * na, max_sweeps, h, m->stream);
+    if (le == cudaSuccess) le = launch_sweep_end(dep, na, d_cum, d_cum + 4 * na, max_sweeps, h, m->stream);
     cudaGraph_t body = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(m->stream, &body);
     e = le != cudaSuccess ? le : ce;
@@ -976,23 +976,23 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   // on 2048-wide batches, the CUDA-core round update is faster (the tile
   // products' operand staging is latency-bound at K = 64)
   const bool tc_apply = !f64 && g_tc_mode == 2;
-  // per problem: 3 counters (zeroed every sweep), the trace, then maxh pair flags
-  // per problem: 3 counters, the trace, the pair flags; then the device-side
-  // loop's cumulative counters (3 per problem + the sweep count), in the
-  // handle's high-water scratch (no allocation once it has grown)
-  const size_t n_dbl = 4 * (size_t)na + ((size_t)na * maxh + 1) / 2;
-  const size_t n_cum = 3 * (size_t)na + 1;
+  // per problem 4 counters (zeroed every sweep), then per problem the trace,
+  // then maxh pair flags per problem; then the device-side loop's cumulative
+  // counters (3 per problem + the sweep count), in the handle's high-water
+  // scratch (no allocation once it has grown)
+  const size_t n_dbl = 5 * (size_t)na + ((size_t)na * maxh + 1) / 2;
+  const size_t n_cum = 4 * (size_t)na + 1;
   TRY(ensure_eig_scratch(m, n_dbl + n_cum));
   double* d_off = m->eig_scr;
   double* d_cum = m->eig_scr + n_dbl;
-  int* d_flag = reinterpret_cast<int*>(d_off + 4 * na);
+  int* d_flag = reinterpret_cast<int*>(d_off + 5 * na);
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
     Work& w = ws[L.act[a]];
     eps[i].G = w.G; eps[i].V = acc[i]; eps[i].J = w.J;
     eps[i].npad = L.nepad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
-    eps[i].off = d_off + 3 * i;
-    eps[i].scale = d_off + 3 * na + i;
+    eps[i].off = d_off + 4 * i;
+    eps[i].scale = d_off + 4 * na + i;
     eps[i].floor_factor = floor_factor;
     eps[i].jflag = d_flag + (size_t)i * maxh;
     eps[i].rel_skip = rel_skip;
@@ -1000,6 +1000,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     if (tc_apply && !w.T) return fail(CTEBD_ERR_STATE, "internal: no round-update scratch");
     if (use_cut) {   // columns sorted by the previous pass: [lo, hi) around the cut
       eps[i].move_rel = 1e-13;
+      eps[i].move_tol = 1e-10;
       eps[i].cut_lo = (int)m->h_res[16 * a + 6];
       eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
     }
@@ -1014,15 +1015,18 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
   }
   const int max_sweeps = g_max_sweeps;
-  auto not_converged = [&](int count) {
+  auto not_converged = [&](int count, double moved) {
+    char tail[96];
+    snprintf(tail, sizeof tail, " (%s pass; the last sweep moved up to %.2e of the trace)",
+             use_cut ? "refinement" : "first", moved);
     return fail(CTEBD_ERR_NUMERIC, "Jacobi eigen-solve: " + std::to_string(count) + " of " +
                                        std::to_string(na) + " problems still rotating after " +
-                                       std::to_string(max_sweeps) + " sweeps");
+                                       std::to_string(max_sweeps) + " sweeps" + tail);
   };
   if (g_sweep_graphs && !m->prof.on) {
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
-    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
     CUDA_TRY(eig_prepare(f64));
     if (tc_apply) CUDA_TRY(eig_apply_tc_prepare());
     std::vector<int> nbs(na);
@@ -1037,24 +1041,26 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     }
     TRY(rc);
     // launches: every sweep runs both halves' rounds (counted as for one batch)
-    const double rounds = hc[3 * na] * (max_nb - 1);
+    const double rounds = hc[4 * na] * (max_nb - 1);
     m->prof.launches[KK_EIG_INNER] += rounds;
     m->prof.launches[KK_EIG_APPLY] += rounds * (tc_apply ? 2 : 1);
     if (tc_apply) m->prof.tc[KK_EIG_APPLY] += rounds * 2;
     for (int i = 0; i < na; i++) {
       // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
-      m->prof.flops[KK_EIG_INNER] += hc[3 * i] * 42.0 * (2 * JB);
-      m->prof.flops[KK_EIG_APPLY] += hc[3 * i + 1];
-      sweeps[sel[i]] += (int)hc[3 * i + 2];
+      m->prof.flops[KK_EIG_INNER] += hc[4 * i] * 42.0 * (2 * JB);
+      m->prof.flops[KK_EIG_APPLY] += hc[4 * i + 1];
+      sweeps[sel[i]] += (int)hc[4 * i + 2];
     }
     int left = 0;
-    for (int i = 0; i < na; i++) left += fin[i].active ? 1 : 0;
-    if (left) return not_converged(left);
+    double moved = 0;
+    for (int i = 0; i < na; i++)
+      if (fin[i].active) { left++; moved = std::max(moved, hc[4 * i + 3]); }
+    if (left) return not_converged(left, moved);
     return CTEBD_OK;
   }
-  std::vector<double> hoff(3 * na);
+  std::vector<double> hoff(5 * na);   // counters, then the traces
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
-    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 3 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
     double fap_sweep = 0, bap_sweep = 0;
     for (int t = 0; t < max_nb - 1; t++) {
       double bin = 0;
@@ -1085,17 +1091,19 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
         }
       }
     }
-    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 5 * na, cudaMemcpyDeviceToHost, m->stream));
     CUDA_TRY(cudaStreamSynchronize(m->stream));
     bool any = false;
     double fap_done = 0;
     for (int i = 0; i < na; i++) {
       if (eps[i].active) sweeps[sel[i]] += 1;
       // inner-solve work: 14 flops per element pair, 3 vectors of length 2JB per rotation
-      m->prof.flops[KK_EIG_INNER] += hoff[3 * i + 1] * 42.0 * (2 * JB);
-      fap_done += hoff[3 * i + 2];
+      m->prof.flops[KK_EIG_INNER] += hoff[4 * i + 1] * 42.0 * (2 * JB);
+      fap_done += hoff[4 * i + 2];
       if (!eps[i].active) continue;
-      if (hoff[3 * i] == 0.0) eps[i].active = 0; else any = true;
+      // same rule as the device-side loop's k_sweep_end
+      const bool settled = eps[i].move_tol > 0 && hoff[4 * i + 3] <= eps[i].move_tol * hoff[4 * na + i];
+      if (hoff[4 * i] == 0.0 || settled) eps[i].active = 0; else any = true;
     }
     m->prof.flops[KK_EIG_APPLY] += fap_done;
     if (fap_sweep > 0) m->prof.bytes[KK_EIG_APPLY] += bap_sweep * (fap_done / fap_sweep);
@@ -1104,8 +1112,10 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     TRY(m->stage.push(eps.data(), eps.size(), &dep));
   }
   int left = 0;
-  for (int i = 0; i < na; i++) left += eps[i].active ? 1 : 0;
-  if (left) return not_converged(left);
+  double moved = 0;
+  for (int i = 0; i < na; i++)
+    if (eps[i].active) { left++; moved = std::max(moved, hoff[4 * i + 3] / hoff[4 * na + i]); }
+  if (left) return not_converged(left, moved);
   return CTEBD_OK;
 }
 

@@ -39,7 +39,8 @@ struct EigProb {
   int nb;       // number of JB-blocks, even
   int active;   // 0: converged, skip
   double* off;         // [0] significant rotations this sweep, [1] all rotations,
-                       // [2] flops of the tile updates actually applied (when jflag set)
+                       // [2] flops of the tile updates actually applied (when jflag set),
+                       // [3] weight the significant rotations moved, sum |t g|
   const double* scale; // trace of G (noise floor of the rotations)
   double floor_factor; // absolute rotation floor = eps * trace * floor_factor
   int* jflag;          // per pair slot: 1 when its J_p is not the identity; null: always apply
@@ -50,6 +51,8 @@ struct EigProb {
                        // [cut_hi, npad) discarded for sure; rotations inside either
                        // set are skipped (they move no weight across the cut)
   void* T;             // npad x npad scratch of the tensor-core round update (FP32)
+  double move_tol;     // > 0: the solve also ends after a sweep whose significant
+                       // rotations moved at most move_tol * trace of weight in all
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -157,10 +160,11 @@ cudaError_t eig_apply_tc_prepare();
 // stream capture of the eigen-solve launches.
 cudaError_t eig_prepare(bool fp64);
 // End of one device-side sweep over n problems (descriptors in device memory,
-// modified in place): add the sweep's counters to cum (3 per problem:
-// rotations, applied flops, sweeps), deactivate converged problems, zero the
-// counters, and let the sweep loop continue while any problem is active and
-// fewer than max_sweeps sweeps ran (count in *n_sweeps).
+// modified in place): add the sweep's counters to cum (4 per problem:
+// rotations, applied flops, sweeps, and the weight the last sweep moved
+// relative to the trace), deactivate converged problems, zero the counters,
+// and let the sweep loop continue while any problem is active and fewer than
+// max_sweeps sweeps ran (count in *n_sweeps).
 cudaError_t launch_sweep_end(EigProb* d_probs, int n, double* cum, double* n_sweeps, int max_sweeps,
                              cudaGraphConditionalHandle h, cudaStream_t s);
 template <typename R>

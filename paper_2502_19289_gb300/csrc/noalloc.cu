@@ -43,7 +43,7 @@ constexpr size_t NA_OFF_RHO = NA_OFF_J + al256((size_t)NA_N * 2 * NA_JB * NA_CPL
 constexpr size_t NA_OFF_PERM = NA_OFF_RHO + al256(2 * NA_N * sizeof(double));   // rho, then |v_i|^2
 constexpr size_t NA_OFF_RES = NA_OFF_PERM + al256(NA_N * sizeof(int));
 constexpr size_t NA_OFF_CNT = NA_OFF_RES + al256(8 * sizeof(double));
-constexpr size_t NA_OFF_DESC = NA_OFF_CNT + al256(4 * sizeof(double));
+constexpr size_t NA_OFF_DESC = NA_OFF_CNT + al256(5 * sizeof(double));
 constexpr size_t NA_DESC_BYTES = 4096;
 constexpr size_t NA_BYTES = NA_OFF_DESC + NA_DESC_BYTES;   // ~2.4 MiB
 
@@ -113,16 +113,18 @@ static int na_gemm(NaDesc& d, const GemmProb& p) {
 // Block-Jacobi on G (npad x npad) accumulating into acc; same kernels and
 // stopping rule as the handle path.
 static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor,
-                  double rel_skip, double move_rel) {
+                  double rel_skip, double move_rel, double move_tol) {
   // [0] significant rotations, [1] all rotations, [2] applied flops (the
-  // kernels' third counter, unused without pair flags), [3] trace of G
+  // kernels' third counter, unused without pair flags), [3] weight moved by
+  // the significant rotations, [4] trace of G
   double* cnt = (double*)(S + NA_OFF_CNT);
   EigProb e{};
   e.G = S + NA_OFF_G; e.V = acc; e.J = S + NA_OFF_J;
   e.npad = npad; e.nb = npad / NA_JB; e.active = 1;
-  e.off = cnt; e.scale = cnt + 3; e.floor_factor = floor_factor;
+  e.off = cnt; e.scale = cnt + 4; e.floor_factor = floor_factor;
   e.rel_skip = rel_skip;   // no pair flags: every tile is updated
   e.move_rel = move_rel;
+  e.move_tol = move_tol;
   const EigProb* de;
   const size_t mark = d.off;
   if (int rc = d.put(&e, 1, &de)) return rc;
@@ -131,15 +133,15 @@ static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor
   const int max_sweeps = max_jacobi_sweeps();
   bool converged = false;
   for (int sweep = 0; sweep < max_sweeps && !converged; sweep++) {
-    NA_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(double), d.s));
+    NA_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(double), d.s));
     for (int t = 0; t < e.nb - 1; t++) {
       NA_CUDA(launch_eig_inner<float>(de, 1, e.nb, t, d.s));
       NA_CUDA(launch_eig_apply<float>(de, 1, e.nb, t, d.s));
     }
-    double h[2] = {0, 0};
+    double h[5] = {0, 0, 0, 0, 0};
     NA_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, d.s));
     NA_CUDA(cudaStreamSynchronize(d.s));
-    converged = h[0] == 0.0;
+    converged = h[0] == 0.0 || (move_tol > 0 && h[3] <= move_tol * h[4]);
   }
   d.off = mark;
   if (!converged)
@@ -212,7 +214,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     if (int rc = na_gemm(d, p)) return rc;
   }
   void* V = S + NA_OFF_V;
-  if (int rc = na_eig(d, S, V, npad, 1.0, 4.0, 0.0)) return rc;
+  if (int rc = na_eig(d, S, V, npad, 1.0, 4.0, 0.0, 0.0)) return rc;
   double res[8];
   auto select = [&](const void* Vc) -> int {
     if (int rc = na_project(d, S, Vc, m, n, npad, lam_l)) return rc;
@@ -243,7 +245,7 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     p.C = S + NA_OFF_G; p.ldc = npad;
     p.kw = lam_l; p.kw_shift = 1; p.alpha = 1.0;
     if (int rc = na_gemm(d, p)) return rc;
-    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0, 1e-13)) return rc;
+    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0, 1e-13, 1e-10)) return rc;
     GemmProb q{};
     q.M = n; q.N = n; q.K = n; q.batch = 1;
     q.A = V; q.lda = npad; q.opA = 0;
