@@ -42,11 +42,11 @@ UNIT = "cluster updates/s"
 # update reads and writes each tile once per 64^3 complex product, so its bytes
 # grow with its flops and the per-flop figure scales to any launch.
 APPLY_TRAFFIC = {
-    "bytes_per_flop": (475024640 + 552518400) / 39868956672.0,
-    "source_sha256": "c44bb9a37c7691cb792bbd36c8dd8912ab3e939cb38920bb7a6e8af5dea6562d",
+    "bytes_per_flop": (474915328 + 552583168) / 39868956672.0,
+    "source_sha256": "d3f456cd52e33ea1c998d4cca88a5959cb948bf7050a961d0b27711949bd845f",
     "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first k_eig_apply_f32 launch of "
                "'bench.py --workload apply-traffic --n 60' on a GB300 (15 problems, widths up to 2048, "
-               "about 1 GB of G and V): 475,024,640 + 552,518,400 B for 3.987e10 algorithmic flops, "
+               "about 1 GB of G and V): 474,915,328 + 552,583,168 B for 3.987e10 algorithmic flops, "
                "scaled to this launch's flops",
 }
 

@@ -1000,7 +1000,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     if (tc_apply && !w.T) return fail(CTEBD_ERR_STATE, "internal: no round-update scratch");
     if (use_cut) {   // columns sorted by the previous pass: [lo, hi) around the cut
       eps[i].move_rel = 1e-13;
-      eps[i].move_tol = 1e-10;
+      // a sweep that moves at most this much weight in all ends the solve:
+      // far below the 1e-5 target on f, and below a hundredth of the cutoff
+      eps[i].move_tol = m->cfg.cutoff > 0 ? std::min(1e-10, 1e-2 * m->cfg.cutoff) : 1e-10;
       eps[i].cut_lo = (int)m->h_res[16 * a + 6];
       eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
     }
@@ -1059,6 +1061,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     return CTEBD_OK;
   }
   std::vector<double> hoff(5 * na);   // counters, then the traces
+  std::vector<double> last_moved(na, 0.0);
+  std::vector<int> sweeps0(na);
+  for (int i = 0; i < na; i++) sweeps0[i] = sweeps[sel[i]];
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
     double fap_sweep = 0, bap_sweep = 0;
@@ -1101,8 +1106,12 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       m->prof.flops[KK_EIG_INNER] += hoff[4 * i + 1] * 42.0 * (2 * JB);
       fap_done += hoff[4 * i + 2];
       if (!eps[i].active) continue;
-      // same rule as the device-side loop's k_sweep_end
-      const bool settled = eps[i].move_tol > 0 && hoff[4 * i + 3] <= eps[i].move_tol * hoff[4 * na + i];
+      // same rules as the device-side loop's k_sweep_end
+      const double moved = hoff[4 * i + 3] / hoff[4 * na + i];
+      if (eps[i].cut_hi > 0 && eps[i].move_tol > 0 && sweeps[sel[i]] - sweeps0[i] >= 6 && moved > 0.9 * last_moved[i])
+        eps[i].cut_hi = 0;
+      last_moved[i] = moved;
+      const bool settled = eps[i].move_tol > 0 && moved <= eps[i].move_tol;
       if (hoff[4 * i] == 0.0 || settled) eps[i].active = 0; else any = true;
     }
     m->prof.flops[KK_EIG_APPLY] += fap_done;
@@ -1114,7 +1123,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   int left = 0;
   double moved = 0;
   for (int i = 0; i < na; i++)
-    if (eps[i].active) { left++; moved = std::max(moved, hoff[4 * i + 3] / hoff[4 * na + i]); }
+    if (eps[i].active) { left++; moved = std::max(moved, last_moved[i]); }
   if (left) return not_converged(left, moved);
   return CTEBD_OK;
 }

@@ -816,8 +816,13 @@ __global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restri
     cum[4 * i] += P.off[1];
     cum[4 * i + 1] += P.off[2];
     cum[4 * i + 2] += 1.0;
-    cum[4 * i + 3] = P.off[3] / (*P.scale);   // weight the last sweep moved, relative to the trace
-    const bool settled = P.move_tol > 0 && P.off[3] <= P.move_tol * (*P.scale);
+    const double moved = P.off[3] / (*P.scale), before = cum[4 * i + 3];
+    cum[4 * i + 3] = moved;   // weight the last sweep moved, relative to the trace
+    // skipped rotations inside the cut's classes leave couplings that rotations
+    // across the cut keep renewing: where the moved weight stalls, rotate every
+    // pair from now on
+    if (P.cut_hi > 0 && P.move_tol > 0 && cum[4 * i + 2] >= 6.0 && moved > 0.9 * before) P.cut_hi = 0;
+    const bool settled = P.move_tol > 0 && moved <= P.move_tol;
     if (P.off[0] == 0.0 || settled) P.active = 0; else any = true;
     P.off[0] = 0.0; P.off[1] = 0.0; P.off[2] = 0.0; P.off[3] = 0.0;
   }

@@ -245,7 +245,8 @@ extern "C" int split2_noalloc(const void* theta, const double* lam_l, int chi_l,
     p.C = S + NA_OFF_G; p.ldc = npad;
     p.kw = lam_l; p.kw_shift = 1; p.alpha = 1.0;
     if (int rc = na_gemm(d, p)) return rc;
-    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0, 1e-13, 1e-10)) return rc;
+    const double move_tol = cutoff > 0 ? std::min(1e-10, 1e-2 * cutoff) : 1e-10;
+    if (int rc = na_eig(d, S, S + NA_OFF_W, npad, 1e-12, 32.0, 1e-13, move_tol)) return rc;
     GemmProb q{};
     q.M = n; q.N = n; q.K = n; q.batch = 1;
     q.A = V; q.lda = npad; q.opA = 0;
