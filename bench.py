@@ -735,7 +735,9 @@ def run_ours(args, rank, world, local_rank):
     res["clocks"] = clk.summary()
     res["steps_detail"] = step_f
     sw = np.concatenate(sweeps) if sweeps else np.zeros((0, 2))
+    capped, capped_moved = mps.solver_stats()
     res["jacobi_sweeps"] = {"splits": int(len(sw)), "cap": P.max_sweeps(),
+                            "refinements_accepted_at_cap": capped, "their_max_moved_rel": capped_moved,
                             "pass1_mean": float(sw[:, 0].mean()) if len(sw) else 0.0,
                             "pass1_max": int(sw[:, 0].max()) if len(sw) else 0,
                             "pass2_mean": float(sw[:, 1].mean()) if len(sw) else 0.0,

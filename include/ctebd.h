@@ -239,6 +239,14 @@ int mps_split_log(const ctebd_mps* mps, double* rows, int cap, int* n_rows);
    check failed) since mps_create: out[0], out[1]. */
 int mps_sketch_stats(const ctebd_mps* mps, double* out);
 
+/* Eigen-solver record since mps_create (not in the paper; the solver of this
+   implementation): out[0] = FP32 refinement passes accepted at the sweep cap
+   (ctebd_set_max_sweeps) because their last sweep moved at most 1e-8 of the
+   trace in weight, out[1] = the largest such last-sweep weight relative to
+   the trace.  A pass left rotating with more than that makes the update fail
+   with CTEBD_ERR_NUMERIC instead.  Errors: ARG. */
+int mps_solver_stats(const ctebd_mps* mps, double* out);
+
 /* ---- Learned rank predictor (sizes the sketched split; not in the paper) ----
    A network F=16 -> 64 -> 64 -> 16 (ReLU, FP32) maps cheap per-split
    features to a bucket b of the ratio rank / Eq.-9 bound, ratio in

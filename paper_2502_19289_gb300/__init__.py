@@ -69,6 +69,7 @@ def _load():
         "mps_load_device": [P, C.POINTER(I), C.POINTER(P), C.POINTER(P)],
         "mps_split_log": [P, C.POINTER(D), I, C.POINTER(I)],
         "mps_sketch_stats": [P, C.POINTER(D)],
+        "mps_solver_stats": [P, C.POINTER(D)],
         "cluster_rank_bounds": [C.POINTER(Gate), I, C.POINTER(Cluster), C.POINTER(I), C.POINTER(I)],
         "ctebd_last_error": [C.c_char_p, S],
         "ctebd_profile": [P, I],
@@ -356,6 +357,13 @@ class MPS:
         out = np.zeros(2)
         _check(_lib.mps_sketch_stats(self._h, _dp(out)), "mps_sketch_stats")
         return int(out[0]), int(out[1])
+
+    def solver_stats(self):
+        """(refinement passes accepted at the sweep cap, their largest
+        last-sweep moved weight relative to the trace)."""
+        out = np.zeros(2)
+        _check(_lib.mps_solver_stats(self._h, _dp(out)), "mps_solver_stats")
+        return int(out[0]), float(out[1])
 
     # --- the cluster update ----------------------------------------------
     def apply_1q(self, q: int, u: np.ndarray):

@@ -395,6 +395,8 @@ struct ctebd_mps {
   std::vector<double> splitlog2;   // per split: sketched, eigen-dim, rank before cap, hint,
                                    // Jacobi sweeps of pass 1 and pass 2
   double sk_stats[2] = {0, 0};     // sketched splits attempted, fallen back
+  double solve_stats[2] = {0, 0};  // refinement passes accepted at the sweep cap, their
+                                   // largest last-sweep moved weight (relative to the trace)
   uint64_t nstep = 0;
   float* mlp = nullptr;            // rank predictor parameters (device)
   int* tc_err = nullptr;           // tensor-core completion-wait timeout flag (device)
@@ -1017,6 +1019,18 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     CUDA_TRY(f64 ? launch_eig_trace<double>(dep, na, m->stream) : launch_eig_trace<float>(dep, na, m->stream));
   }
   const int max_sweeps = g_max_sweeps;
+  // A refinement pass whose last sweep moved at most kCapAccept of the trace
+  // is accepted at the sweep cap (the split's f is then exact to about that
+  // level, far below 1e-5) and counted in solve_stats; anything else left
+  // rotating is an error.
+  constexpr double kCapAccept = 1e-8;
+  auto capped = [&](int i, double moved) {
+    if (!use_cut || !(moved <= kCapAccept)) return false;
+    m->solve_stats[0] += 1;
+    m->solve_stats[1] = std::max(m->solve_stats[1], moved);
+    (void)i;
+    return true;
+  };
   auto not_converged = [&](int count, double moved) {
     char tail[96];
     snprintf(tail, sizeof tail, " (%s pass; the last sweep moved up to %.2e of the trace)",
@@ -1056,7 +1070,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     int left = 0;
     double moved = 0;
     for (int i = 0; i < na; i++)
-      if (fin[i].active) { left++; moved = std::max(moved, hc[4 * i + 3]); }
+      if (fin[i].active && !capped(i, hc[4 * i + 3])) { left++; moved = std::max(moved, hc[4 * i + 3]); }
     if (left) return not_converged(left, moved);
     return CTEBD_OK;
   }
@@ -1123,7 +1137,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   int left = 0;
   double moved = 0;
   for (int i = 0; i < na; i++)
-    if (eps[i].active) { left++; moved = std::max(moved, last_moved[i]); }
+    if (eps[i].active && !capped(i, last_moved[i])) { left++; moved = std::max(moved, last_moved[i]); }
   if (left) return not_converged(left, moved);
   return CTEBD_OK;
 }
@@ -1891,6 +1905,13 @@ extern "C" int mps_split_log(const ctebd_mps* m, double* rows, int cap, int* n_r
       std::memcpy(rows + 14 * i, m->splitlog.data() + 8 * i, sizeof(double) * 8);
       std::memcpy(rows + 14 * i + 8, m->splitlog2.data() + 6 * i, sizeof(double) * 6);
     }
+  return CTEBD_OK;
+}
+
+extern "C" int mps_solver_stats(const ctebd_mps* m, double* out) {
+  if (!m || !out) return fail(CTEBD_ERR_ARG, "mps_solver_stats: null argument");
+  out[0] = m->solve_stats[0];
+  out[1] = m->solve_stats[1];
   return CTEBD_OK;
 }
 
