@@ -1418,7 +1418,11 @@ static int level_solve(ctebd_mps* m, std::vector<Work>& ws, Level& L, const std:
   // sweeps going only if it moves more than 1e-13 of the total weight: among
   // directions whose weights sit at the rounding level the relative test
   // alone never settles, and what such rotations leave unmoved is below
-  // n^2 / 2 * 1e-13 of the total.
+  // n^2 / 2 * 1e-13 of the total.  The pass also ends after a sweep whose
+  // significant rotations moved at most min(1e-10, cutoff / 100) of the total
+  // in all; a problem whose moved weight stalls rotates every pair from then
+  // on (the skipped classes below otherwise keep renewing couplings across
+  // the cut); see level_eig for the sweep cap.
   //
   // The kept weight is a sum over the kept set and the tail a sum over the
   // discarded set, so rotations within either set change neither.  With the

@@ -194,23 +194,23 @@ template <typename R>
 __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict__ probs, int round) {
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, NBLK = JB * (JB + 1) / 2;
-  // per thread: A blocks (all 256 threads); Q rows (warps 1-7, rows row0 + j QSTEP)
-  constexpr int NB_T = (NBLK + 255) / 256, QSTEP = 224 / JB, QROWS = (D + QSTEP - 1) / QSTEP;
+  // per thread: A blocks; Q rows row0 + j QSTEP (one rotation per thread)
+  constexpr int NB_T = (NBLK + 255) / 256, QSTEP = 256 / JB, QROWS = D / QSTEP;
   constexpr unsigned PMASK = JB == 32 ? 0xffffffffu : ((1u << JB) - 1u);   // lanes of the parameter phase
-  static_assert(224 % JB == 0, "inner kernel: 256 threads");
+  static_assert(256 % JB == 0 && D % QSTEP == 0, "inner kernel: 256 threads");
   const EigProb P = probs[blockIdx.y];
   if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2) return;
   extern __shared__ unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
   CT* Q = A + D * LD;
-  // rotation parameters, two sets (round r uses set r & 1): tan(theta / 2),
-  // sin(theta), phase, and the pair (p, q) of each of the JB rotations
+  // rotation parameters of the round: tan(theta / 2), sin(theta), phase, and
+  // the pair (p, q) of each of the JB rotations
   R* tu = reinterpret_cast<R*>(Q + D * LD);
-  R* sn = tu + 2 * JB;
-  CT* ph = reinterpret_cast<CT*>(sn + 2 * JB);
-  int* pp = reinterpret_cast<int*>(ph + 2 * JB);
-  int* pq = pp + 2 * JB;
-  unsigned short* blk = reinterpret_cast<unsigned short*>(pq + 2 * JB);   // pair blocks a <= b: a | b << 8
+  R* sn = tu + JB;
+  CT* ph = reinterpret_cast<CT*>(sn + JB);
+  int* pp = reinterpret_cast<int*>(ph + JB);
+  int* pq = pp + JB;
+  unsigned short* blk = reinterpret_cast<unsigned short*>(pq + JB);   // pair blocks a <= b: a | b << 8
   __shared__ int nrot, nsig;
   __shared__ double nmove;   // weight moved by this sweep's significant rotations
   int I, J;
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   __syncthreads();
   int total = 0, total_sig = 0;
   const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
-  // rotations of round r into parameter set st (the first JB lanes of warp 0)
-  auto params = [&](int r, int st) {
+  // rotations of round r (the first JB lanes of warp 0)
+  auto params = [&](int r) {
     if (threadIdx.x < JB) {
       int p, q;
       circle(r, threadIdx.x, D, p, q);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
           skip = true; sig = false; c = 1; s = 0; e = cmk<CT>(1, 0);
         }
       }
-      const int o = st * JB + threadIdx.x;
+      const int o = threadIdx.x;
       pp[o] = p; pq[o] = q;
       tu[o] = s / ((R)1 + c); sn[o] = s; ph[o] = e;
       // rotation counters and moved weight: one shared-memory update per
@@ -275,23 +275,18 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     if (threadIdx.x == 0) { nrot = 0; nsig = 0; nmove = 0.0; }
     __syncthreads();
-    params(0, 0);
-    __syncthreads();
     for (int r = 0; r < D - 1; r++) {
-      const R* tu_r = tu + (r & 1) * JB;
-      const R* sn_r = sn + (r & 1) * JB;
-      const CT* ph_r = ph + (r & 1) * JB;
-      const int* pp_r = pp + (r & 1) * JB;
-      const int* pq_r = pq + (r & 1) * JB;
-      // A <- R^H A R, every rotation in Rutishauser's form
+      params(r);
+      __syncthreads();
+      // A <- R^H A R and Q <- Q R, every rotation in Rutishauser's form
       //   x' = x - s (y + tau x),  y' = y + s (x - tau y),  tau = s / (1 + c):
       // for small angles c = 1 - s tau is not rounded to 1, which would grow
       // every vector by (1 + t^2) per rotation in FP32.  The rotations of a
       // round act on disjoint pairs, so the 2 x 2 block of A on pairs (a, b)
       // becomes R_a^H B R_b by itself: one thread per block with a <= b, the
       // block below the diagonal is its conjugate transpose (A stays Hermitian).
-      // Every element a thread touches is its own, so all of its loads are
-      // issued before any arithmetic or store.
+      // Every element a thread touches in a round is its own, so all of its
+      // loads (A blocks, Q pairs) are issued before any arithmetic or store.
       int ia[NB_T], ib[NB_T];
       CT x00[NB_T], x10[NB_T], x01[NB_T], x11[NB_T];
 #pragma unroll
@@ -300,24 +295,33 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
         const int bb = e < NBLK ? blk[e] : 0;
         ia[u] = bb & 0xff;
         ib[u] = bb >> 8;
-        const int pa = pp_r[ia[u]], qa = pq_r[ia[u]], pb = pp_r[ib[u]], qb = pq_r[ib[u]];
+        const int pa = pp[ia[u]], qa = pq[ia[u]], pb = pp[ib[u]], qb = pq[ib[u]];
         x00[u] = A[pa * LD + pb]; x10[u] = A[qa * LD + pb];
         x01[u] = A[pa * LD + qb]; x11[u] = A[qa * LD + qb];
+      }
+      const int kq = threadIdx.x % JB, row0 = threadIdx.x / JB;
+      const int cp = pp[kq], cq = pq[kq];
+      CT xq[QROWS], yq[QROWS];
+#pragma unroll
+      for (int j = 0; j < QROWS; j++) {
+        const int row = row0 + j * QSTEP;
+        xq[j] = Q[row * LD + cp];
+        yq[j] = Q[row * LD + cq];
       }
 #pragma unroll
       for (int u = 0; u < NB_T; u++) {
         if (threadIdx.x + 256 * u >= NBLK) continue;
         const int a = ia[u], b = ib[u];
-        const int pa = pp_r[a], qa = pq_r[a], pb = pp_r[b], qb = pq_r[b];
-        const R tb = tu_r[b], sb = sn_r[b];
-        const CT fb = ph_r[b];
+        const int pa = pp[a], qa = pq[a], pb = pp[b], qb = pq[b];
+        const R tb = tu[b], sb = sn[b];
+        const CT fb = ph[b];
         const CT y0 = cmul(x01[u], fb), y1 = cmul(x11[u], fb);
         const CT n00 = cmk<CT>(x00[u].x - sb * (y0.x + tb * x00[u].x), x00[u].y - sb * (y0.y + tb * x00[u].y));
         const CT n01 = cmk<CT>(y0.x + sb * (x00[u].x - tb * y0.x), y0.y + sb * (x00[u].y - tb * y0.y));
         const CT n10 = cmk<CT>(x10[u].x - sb * (y1.x + tb * x10[u].x), x10[u].y - sb * (y1.y + tb * x10[u].y));
         const CT n11 = cmk<CT>(y1.x + sb * (x10[u].x - tb * y1.x), y1.y + sb * (x10[u].y - tb * y1.y));
-        const R ta = tu_r[a], sa = sn_r[a];
-        const CT fa = cconj(ph_r[a]);
+        const R ta = tu[a], sa = sn[a];
+        const CT fa = cconj(ph[a]);
         const CT z0 = cmul(n10, fa), z1 = cmul(n11, fa);
         const CT m00 = cmk<CT>(n00.x - sa * (z0.x + ta * n00.x), n00.y - sa * (z0.y + ta * n00.y));
         const CT m10 = cmk<CT>(z0.x + sa * (n00.x - ta * z0.x), z0.y + sa * (n00.y - ta * z0.y));
@@ -330,30 +334,15 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
           A[pb * LD + qa] = cconj(m10); A[qb * LD + qa] = cconj(m11);
         }
       }
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        // warp 0: the next round's rotations from the updated A
-        if (r + 1 < D - 1) params(r + 1, (r + 1) & 1);
-      } else {
-        // warps 1-7: Q <- Q R (columns p, q of each rotation), one rotation per thread
-        const int tq = threadIdx.x - 32, kq = tq % JB, row0 = tq / JB;
-        const int cp = pp_r[kq], cq = pq_r[kq];
-        const R t = tu_r[kq], s = sn_r[kq];
-        const CT f = ph_r[kq];
-        CT xq[QROWS], yq[QROWS];
+      {
+        const R t = tu[kq], s = sn[kq];
+        const CT f = ph[kq];
 #pragma unroll
         for (int j = 0; j < QROWS; j++) {
           const int row = row0 + j * QSTEP;
-          if (row < D) { xq[j] = Q[row * LD + cp]; yq[j] = Q[row * LD + cq]; }
-        }
-#pragma unroll
-        for (int j = 0; j < QROWS; j++) {
-          const int row = row0 + j * QSTEP;
-          if (row < D) {
-            const CT x = xq[j], y = cmul(yq[j], f);
-            Q[row * LD + cp] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
-            Q[row * LD + cq] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
-          }
+          const CT x = xq[j], y = cmul(yq[j], f);
+          Q[row * LD + cp] = cmk<CT>(x.x - s * (y.x + t * x.x), x.y - s * (y.y + t * x.y));
+          Q[row * LD + cq] = cmk<CT>(y.x + s * (x.x - t * y.x), y.y + s * (x.y - t * y.y));
         }
       }
       __syncthreads();
@@ -753,7 +742,7 @@ static void eig_attrs() {
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
   static bool attr = false;
   if (attr) return;
-  const size_t sm_inner = 2 * sizeof(CT) * D * LD + 2 * JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
                           sizeof(unsigned short) * JB * (JB + 1) / 2;
   const size_t sm_apply = 2 * sizeof(CT) * D * LD;
   cudaFuncSetAttribute(k_eig_inner<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
@@ -766,7 +755,7 @@ cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, in
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1;
   eig_attrs<R>();
-  const size_t sm_inner = 2 * sizeof(CT) * D * LD + 2 * JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
+  const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
                           sizeof(unsigned short) * JB * (JB + 1) / 2;
   k_eig_inner<R><<<dim3(max_nb / 2, n_probs), 256, sm_inner, s>>>(d_probs, round);
   return cudaGetLastError();
