@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   int* pq = pp + JB;
   unsigned short* blk = reinterpret_cast<unsigned short*>(pq + JB);   // pair blocks a <= b: a | b << 8
   __shared__ int nrot, nsig;
-  __shared__ double nmove;   // weight moved by this sweep's significant rotations
+  __shared__ R nmove;   // weight moved by this sweep's significant rotations
   int I, J;
   circle(round, blockIdx.x, P.nb, I, J);
   const bool cut = P.cut_hi > 0 && P.jflag;
@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   const R floor_abs = (R)((double)eps_r * (*P.scale) * P.floor_factor);
   const R rel_skip = P.rel_skip > 0 ? (R)P.rel_skip : (R)4;
   const R move_abs = (R)(P.move_rel * (*P.scale));
+  const bool track_move = P.move_tol > 0;   // the solve's moved-weight stopping rule
   __syncthreads();
   int total = 0, total_sig = 0;
   const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
@@ -248,10 +249,13 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
       circle(r, threadIdx.x, D, p, q);
       R c, s; CT e; bool skip, sig;
       jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip, sig);
-      // the rotation moves |t g| of weight between p and q (t = s / c)
-      const CT g = A[p * LD + q];
-      const R mv = fabs(s) * sqrt(g.x * g.x + g.y * g.y) / c;
-      if (sig && move_abs > 0 && !(mv > move_abs)) sig = false;
+      R mv = 0;   // the weight the rotation moves between p and q, |t g| (t = s / c)
+      if (sig && move_abs > 0) {
+        const CT g = A[p * LD + q];
+        const R sg = fabs(s) * sqrt(g.x * g.x + g.y * g.y);
+        if (!(sg > move_abs * c)) sig = false;
+        else if (track_move) mv = sg / c;
+      }
       if (cut) {
         const int gp = p < JB ? I * JB + p : J * JB + p - JB;
         const int gq = q < JB ? I * JB + q : J * JB + q - JB;
@@ -262,18 +266,21 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
       const int o = threadIdx.x;
       pp[o] = p; pq[o] = q;
       tu[o] = s / ((R)1 + c); sn[o] = s; ph[o] = e;
-      // rotation counters and moved weight: one shared-memory update per
-      // round, by lane 0
+      // rotation counters (and the moved weight): one shared-memory update
+      // per round, by lane 0
       const unsigned mr = __ballot_sync(PMASK, !skip), ms = __ballot_sync(PMASK, sig);
-      double mw = sig ? (double)mv : 0.0;
+      if (track_move) {
+        R mw = sig ? mv : (R)0;
 #pragma unroll
-      for (int o = JB / 2; o > 0; o >>= 1) mw += __shfl_xor_sync(PMASK, mw, o);
-      if (threadIdx.x == 0) { nrot += __popc(mr); nsig += __popc(ms); nmove += mw; }
+        for (int o = JB / 2; o > 0; o >>= 1) mw += __shfl_xor_sync(PMASK, mw, o);
+        if (threadIdx.x == 0) nmove += mw;
+      }
+      if (threadIdx.x == 0) { nrot += __popc(mr); nsig += __popc(ms); }
     }
   };
   double last_move = 0.0;
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
-    if (threadIdx.x == 0) { nrot = 0; nsig = 0; nmove = 0.0; }
+    if (threadIdx.x == 0) { nrot = 0; nsig = 0; nmove = 0; }
     __syncthreads();
     for (int r = 0; r < D - 1; r++) {
       params(r);
@@ -350,7 +357,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
     const int nr = nrot;
     total += nr;
     total_sig += nsig;
-    last_move = nmove;
+    last_move = (double)nmove;
     __syncthreads();
     if (nr == 0) break;
   }
