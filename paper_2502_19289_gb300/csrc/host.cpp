@@ -894,8 +894,14 @@ extern "C" int ctebd_set_sweep_graphs(int on) {
 // body holds two independent chains of round launches (joined before the
 // sweep-end kernel), so one half's latency-bound inner kernels can run while
 // the other half's apply kernels do.
+// Batches of more than kSweepCompact problems get a second chain of round
+// launches over a compact copy of the problems still active (grid y =
+// kSweepCompact): the last sweeps of a batch typically rotate one or two
+// problems, and the full grids' early-exiting CTAs then cost more than the work.
+constexpr int kSweepCompact = 8;
+
 static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector<int>& nbs, double* d_cum,
-                           int max_sweeps, bool tc_apply) {
+                           int max_sweeps, bool tc_apply, EigProb* d_compact, int* d_mode) {
   const bool f64 = m->fp64;
   if (!m->side) {
     CUDA_TRY(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
@@ -905,16 +911,51 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector
   const int na0 = na > 1 ? (na + 1) / 2 : na, na1 = na - na0;
   int nb0 = 2, nb1 = 2;
   for (int i = 0; i < na; i++) (i < na0 ? nb0 : nb1) = std::max(i < na0 ? nb0 : nb1, nbs[i]);
+  const int max_nb = std::max(nb0, nb1);
   const int JB = eig_block(f64);
-  auto chain = [&](EigProb* d, int n, int max_nb, cudaStream_t s) -> cudaError_t {
+  const bool compact = na > kSweepCompact && d_compact && d_mode;
+  auto chain = [&](EigProb* d, int n, int mnb, cudaStream_t s) -> cudaError_t {
     cudaError_t le = cudaSuccess;
-    for (int t = 0; t < max_nb - 1 && le == cudaSuccess; t++) {
-      le = f64 ? launch_eig_inner<double>(d, n, max_nb, t, s) : launch_eig_inner<float>(d, n, max_nb, t, s);
+    for (int t = 0; t < mnb - 1 && le == cudaSuccess; t++) {
+      le = f64 ? launch_eig_inner<double>(d, n, mnb, t, s) : launch_eig_inner<float>(d, n, mnb, t, s);
       if (le != cudaSuccess) break;
-      if (tc_apply) le = launch_eig_apply_tc(d, n, max_nb, max_nb * JB, t, m->tc_err, s);
-      else le = f64 ? launch_eig_apply<double>(d, n, max_nb, t, s) : launch_eig_apply<float>(d, n, max_nb, t, s);
+      if (tc_apply) le = launch_eig_apply_tc(d, n, mnb, mnb * JB, t, m->tc_err, s);
+      else le = f64 ? launch_eig_apply<double>(d, n, mnb, t, s) : launch_eig_apply<float>(d, n, mnb, t, s);
     }
     return le;
+  };
+  // both halves of the batch, the second on the side stream (fork / join)
+  auto full_chains = [&]() -> cudaError_t {
+    cudaError_t le = cudaSuccess;
+    if (na1 > 0) {
+      le = cudaEventRecord(m->fork_ev, m->stream);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(m->side, m->fork_ev, 0);
+      if (le == cudaSuccess) le = chain(dep + na0, na1, nb1, m->side);
+      if (le == cudaSuccess) le = cudaEventRecord(m->join_ev, m->side);
+    }
+    if (le == cudaSuccess) le = chain(dep, na0, nb0, m->stream);
+    if (le == cudaSuccess && na1 > 0) le = cudaStreamWaitEvent(m->stream, m->join_ev, 0);
+    return le;
+  };
+  // capture fn's launches on the handle's stream into graph gr after deps
+  auto capture = [&](cudaGraph_t gr, const cudaGraphNode_t* deps, size_t nd, auto fn) -> cudaError_t {
+    cudaError_t ce = cudaStreamBeginCaptureToGraph(m->stream, gr, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ce;
+    const cudaError_t le = fn();
+    cudaGraph_t out = nullptr;
+    ce = cudaStreamEndCapture(m->stream, &out);
+    return le != cudaSuccess ? le : ce;
+  };
+  auto add_if = [&](cudaGraph_t parent, const cudaGraphNode_t* dep_node, cudaGraphConditionalHandle hh,
+                    cudaGraphNode_t* out_node, cudaGraph_t* out_body) -> cudaError_t {
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hh;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    const cudaError_t ce = cudaGraphAddNode(out_node, parent, dep_node, nullptr, dep_node ? 1 : 0, &ip);
+    if (ce == cudaSuccess) *out_body = ip.conditional.phGraph_out[0];
+    return ce;
   };
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
@@ -930,23 +971,35 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector
     cp.conditional.size = 1;
     e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
   }
-  if (e == cudaSuccess)
-    e = cudaStreamBeginCaptureToGraph(m->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaError_t le = cudaSuccess;
-    if (na1 > 0) {   // fork the second half onto the side stream
-      le = cudaEventRecord(m->fork_ev, m->stream);
-      if (le == cudaSuccess) le = cudaStreamWaitEvent(m->side, m->fork_ev, 0);
-      if (le == cudaSuccess) le = chain(dep + na0, na1, nb1, m->side);
-      if (le == cudaSuccess) le = cudaEventRecord(m->join_ev, m->side);
+  if (e == cudaSuccess && !compact) {
+    e = capture(cp.conditional.phGraph_out[0], nullptr, 0, [&]() -> cudaError_t {
+      cudaError_t le = full_chains();
+      if (le == cudaSuccess)
+        le = launch_sweep_end(dep, na, d_cum, d_cum + 4 * na, max_sweeps, h, nullptr, 0, nullptr, m->stream);
+      return le;
+    });
+  } else if (e == cudaSuccess) {
+    // body: sweep_begin -> IF compact { one chain } -> IF full { both halves } -> sweep_end
+    cudaGraph_t body = cp.conditional.phGraph_out[0], bc = nullptr, bf = nullptr;
+    cudaGraphConditionalHandle hc{}, hf{};
+    cudaGraphNode_t n_begin = nullptr, n_c = nullptr, n_f = nullptr;
+    e = cudaGraphConditionalHandleCreate(&hc, body, 0, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hf, body, 0, 0);
+    if (e == cudaSuccess) e = capture(body, nullptr, 0, [&]() { return launch_sweep_begin(d_mode, hc, hf, m->stream); });
+    if (e == cudaSuccess) {
+      size_t nn = 1;
+      e = cudaGraphGetNodes(body, &n_begin, &nn);
+      if (e == cudaSuccess && nn != 1) e = cudaErrorUnknown;
     }
-    if (le == cudaSuccess) le = chain(dep, na0, nb0, m->stream);
-    if (le == cudaSuccess && na1 > 0) le = cudaStreamWaitEvent(m->stream, m->join_ev, 0);
-    if (le == cudaSuccess) le = launch_sweep_end(dep, na, d_cum, d_cum + 4 * na, max_sweeps, h, m->stream);
-    cudaGraph_t body = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(m->stream, &body);
-    e = le != cudaSuccess ? le : ce;
+    if (e == cudaSuccess) e = add_if(body, &n_begin, hc, &n_c, &bc);
+    if (e == cudaSuccess) e = capture(bc, nullptr, 0, [&]() { return chain(d_compact, kSweepCompact, max_nb, m->stream); });
+    if (e == cudaSuccess) e = add_if(body, &n_c, hf, &n_f, &bf);
+    if (e == cudaSuccess) e = capture(bf, nullptr, 0, full_chains);
+    if (e == cudaSuccess)
+      e = capture(body, &n_f, 1, [&]() {
+        return launch_sweep_end(dep, na, d_cum, d_cum + 4 * na, max_sweeps, h, d_compact, kSweepCompact, d_mode,
+                                m->stream);
+      });
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
   if (e == cudaSuccess) e = cudaGraphLaunch(ex, m->stream);
@@ -984,9 +1037,13 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   // scratch (no allocation once it has grown)
   const size_t n_dbl = 5 * (size_t)na + ((size_t)na * maxh + 1) / 2;
   const size_t n_cum = 4 * (size_t)na + 1;
-  TRY(ensure_eig_scratch(m, n_dbl + n_cum));
+  // the sweep graph's compact descriptor copies and chain selector
+  const size_t n_cmp = (kSweepCompact * sizeof(EigProb) + sizeof(double)) / sizeof(double) + 1;
+  TRY(ensure_eig_scratch(m, n_dbl + n_cum + n_cmp));
   double* d_off = m->eig_scr;
   double* d_cum = m->eig_scr + n_dbl;
+  EigProb* d_compact = reinterpret_cast<EigProb*>(m->eig_scr + n_dbl + n_cum);
+  int* d_mode = reinterpret_cast<int*>(d_compact + kSweepCompact);
   int* d_flag = reinterpret_cast<int*>(d_off + 5 * na);
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
@@ -1043,11 +1100,13 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_mode, 0, sizeof(int), m->stream));   // first sweep: the full chain
     CUDA_TRY(eig_prepare(f64));
     if (tc_apply) CUDA_TRY(eig_apply_tc_prepare());
     std::vector<int> nbs(na);
     for (int i = 0; i < na; i++) nbs[i] = eps[i].nb;
-    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps, tc_apply);
+    const int rc = run_sweep_graph(m, const_cast<EigProb*>(dep), na, nbs, d_cum, max_sweeps, tc_apply, d_compact,
+                                   d_mode);
     std::vector<double> hc(n_cum, 0.0);
     std::vector<EigProb> fin(na);   // descriptors after the loop: active = still rotating
     if (rc == CTEBD_OK) {

@@ -165,8 +165,15 @@ cudaError_t eig_prepare(bool fp64);
 // relative to the trace), deactivate converged problems, zero the counters,
 // and let the sweep loop continue while any problem is active and fewer than
 // max_sweeps sweeps ran (count in *n_sweeps).
+// With compact != null, the problems still active are also copied to
+// compact[0 .. compact_cap) when they fit, and *mode = 1 (else 0).
 cudaError_t launch_sweep_end(EigProb* d_probs, int n, double* cum, double* n_sweeps, int max_sweeps,
-                             cudaGraphConditionalHandle h, cudaStream_t s);
+                             cudaGraphConditionalHandle h, EigProb* compact, int compact_cap, int* mode,
+                             cudaStream_t s);
+// Sets the two conditional handles of a sweep body from *mode: h_compact =
+// mode, h_full = !mode.
+cudaError_t launch_sweep_begin(const int* mode, cudaGraphConditionalHandle h_compact,
+                               cudaGraphConditionalHandle h_full, cudaStream_t s);
 template <typename R>
 cudaError_t launch_eig_trace(const EigProb* d_probs, int n_probs, cudaStream_t s);
 

@@ -801,11 +801,16 @@ cudaError_t eig_prepare(bool fp64) {
   return cudaGetLastError();
 }
 
-// One thread walks the problems (a few hundred at most per batch).
+// One thread walks the problems (a few hundred at most per batch).  With a
+// compact array, the problems still active after the sweep are also copied
+// there when they fit (the copies point at the same buffers and counters),
+// and *mode tells the next sweep which chain of launches to run.
 __global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restrict__ cum,
-                            double* __restrict__ n_sweeps, int max_sweeps, cudaGraphConditionalHandle h) {
+                            double* __restrict__ n_sweeps, int max_sweeps, cudaGraphConditionalHandle h,
+                            EigProb* __restrict__ compact, int compact_cap, int* __restrict__ mode) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   bool any = false;
+  int n_active = 0;
   for (int i = 0; i < n; i++) {
     EigProb& P = probs[i];
     if (!P.active) continue;
@@ -819,16 +824,43 @@ __global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restri
     // pair from now on
     if (P.cut_hi > 0 && P.move_tol > 0 && cum[4 * i + 2] >= 6.0 && moved > 0.9 * before) P.cut_hi = 0;
     const bool settled = P.move_tol > 0 && moved <= P.move_tol;
-    if (P.off[0] == 0.0 || settled) P.active = 0; else any = true;
+    if (P.off[0] == 0.0 || settled) P.active = 0; else { any = true; n_active++; }
     P.off[0] = 0.0; P.off[1] = 0.0; P.off[2] = 0.0; P.off[3] = 0.0;
   }
   *n_sweeps += 1.0;
+  if (compact) {
+    const bool fit = n_active <= compact_cap;
+    if (fit) {
+      int c = 0;
+      for (int i = 0; i < n; i++)
+        if (probs[i].active) compact[c++] = probs[i];
+      for (; c < compact_cap; c++) compact[c].active = 0;
+    }
+    *mode = fit ? 1 : 0;
+  }
   cudaGraphSetConditional(h, (any && *n_sweeps < (double)max_sweeps) ? 1u : 0u);
 }
 
+// First node of a device-side sweep: run the compact chain (mode 1) or the
+// full one (mode 0).
+__global__ void k_sweep_begin(const int* __restrict__ mode, cudaGraphConditionalHandle h_compact,
+                              cudaGraphConditionalHandle h_full) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned m = *mode != 0 ? 1u : 0u;
+  cudaGraphSetConditional(h_compact, m);
+  cudaGraphSetConditional(h_full, 1u - m);
+}
+
 cudaError_t launch_sweep_end(EigProb* d_probs, int n, double* cum, double* n_sweeps, int max_sweeps,
-                             cudaGraphConditionalHandle h, cudaStream_t s) {
-  k_sweep_end<<<1, 32, 0, s>>>(d_probs, n, cum, n_sweeps, max_sweeps, h);
+                             cudaGraphConditionalHandle h, EigProb* compact, int compact_cap, int* mode,
+                             cudaStream_t s) {
+  k_sweep_end<<<1, 32, 0, s>>>(d_probs, n, cum, n_sweeps, max_sweeps, h, compact, compact_cap, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_begin(const int* mode, cudaGraphConditionalHandle h_compact,
+                               cudaGraphConditionalHandle h_full, cudaStream_t s) {
+  k_sweep_begin<<<1, 32, 0, s>>>(mode, h_compact, h_full);
   return cudaGetLastError();
 }
 
