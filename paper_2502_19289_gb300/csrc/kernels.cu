@@ -875,31 +875,44 @@ template cudaError_t launch_eig_apply<double>(const EigProb*, int, int, int, cud
 // Weighted column norms rho_i = sum_row lambda_L[row >> shift]^2 |R[row][i]|^2
 // in FP64: the Schmidt weight carried by direction i (Eq. 4 terms).
 // ---------------------------------------------------------------------------
-constexpr int CN_ROWS = 256;
+// One CTA of 256 threads per 32 columns: warp w sums rows w, w + 8, ... of
+// its lane's column (a warp reads 32 consecutive elements of a row), then the
+// eight partial sums are added in a fixed order -- the result does not depend
+// on the order in which CTAs run (ties between weights decide the sort order
+// of the directions, so rho must be reproducible bit for bit).
+constexpr int CN_COLS = 32, CN_WARPS = 8;
 
 template <typename R>
-__global__ void k_colnorm(const void* const* __restrict__ Rs, const int* __restrict__ ms,
-                          const int* __restrict__ ns, const int* __restrict__ lds,
-                          const double* const* __restrict__ lams, const int* __restrict__ shifts,
-                          double* const* __restrict__ rhos) {
+__global__ void __launch_bounds__(CN_COLS * CN_WARPS) k_colnorm(
+    const void* const* __restrict__ Rs, const int* __restrict__ ms, const int* __restrict__ ns,
+    const int* __restrict__ lds, const double* const* __restrict__ lams, const int* __restrict__ shifts,
+    double* const* __restrict__ rhos) {
   using CT = typename C2<R>::T;
-  const int p = blockIdx.z;
+  __shared__ double part[CN_WARPS][CN_COLS];
+  const int p = blockIdx.y;
   const int n = ns[p], m = ms[p];
+  const int c0 = blockIdx.x * CN_COLS;
+  if (c0 >= n) return;
   const long long ld = lds ? lds[p] : n;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r0 = blockIdx.y * CN_ROWS;
-  if (c >= n || r0 >= m) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c = c0 + lane;
   const CT* Rm = (const CT*)Rs[p];
   const double* lam = lams[p];
   const int sh = shifts[p];
-  const int r1 = min(m, r0 + CN_ROWS);
   double acc = 0;
-  for (int r = r0; r < r1; r++) {
-    const CT v = Rm[(long long)r * ld + c];
-    const double w = lam ? lam[r >> sh] : 1.0;
-    acc += w * w * ((double)v.x * v.x + (double)v.y * v.y);
+  if (c < n)
+    for (int r = w; r < m; r += CN_WARPS) {
+      const CT v = Rm[(long long)r * ld + c];
+      const double wt = lam ? lam[r >> sh] : 1.0;
+      acc += wt * wt * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+  part[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && c < n) {
+    double t = 0;
+#pragma unroll
+    for (int k = 0; k < CN_WARPS; k++) t += part[k][lane];
+    rhos[p][c] = t;
   }
-  atomicAdd(&rhos[p][c], acc);
 }
 
 template <typename R>
@@ -908,8 +921,9 @@ cudaError_t launch_colnorm_batch(const void* const* d_R, const int* d_m, const i
                                  double* const* d_rho, int n_probs, int max_n, int max_m,
                                  cudaStream_t s) {
   if (n_probs <= 0) return cudaSuccess;
-  dim3 grid((max_n + 127) / 128, (max_m + CN_ROWS - 1) / CN_ROWS, n_probs);
-  k_colnorm<R><<<grid, 128, 0, s>>>(d_R, d_m, d_n, d_ld, d_lam, d_shift, d_rho);
+  (void)max_m;
+  dim3 grid((max_n + CN_COLS - 1) / CN_COLS, n_probs);
+  k_colnorm<R><<<grid, CN_COLS * CN_WARPS, 0, s>>>(d_R, d_m, d_n, d_ld, d_lam, d_shift, d_rho);
   return cudaGetLastError();
 }
 template cudaError_t launch_colnorm_batch<float>(const void* const*, const int*, const int*, const int*,
