@@ -1035,7 +1035,8 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   // then maxh pair flags per problem; then the device-side loop's cumulative
   // counters (3 per problem + the sweep count), in the handle's high-water
   // scratch (no allocation once it has grown)
-  const size_t n_dbl = 5 * (size_t)na + ((size_t)na * maxh + 1) / 2;
+  const size_t n_mv = (size_t)na * maxh;   // per problem and pair slot: moved weight of the sweep
+  const size_t n_dbl = 5 * (size_t)na + n_mv + ((size_t)na * maxh + 1) / 2;
   const size_t n_cum = 4 * (size_t)na + 1;
   // the sweep graph's compact descriptor copies and chain selector
   const size_t n_cmp = (kSweepCompact * sizeof(EigProb) + sizeof(double)) / sizeof(double) + 1;
@@ -1044,7 +1045,8 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
   double* d_cum = m->eig_scr + n_dbl;
   EigProb* d_compact = reinterpret_cast<EigProb*>(m->eig_scr + n_dbl + n_cum);
   int* d_mode = reinterpret_cast<int*>(d_compact + kSweepCompact);
-  int* d_flag = reinterpret_cast<int*>(d_off + 5 * na);
+  double* d_mv = d_off + 5 * na;
+  int* d_flag = reinterpret_cast<int*>(d_mv + n_mv);
   for (int i = 0; i < na; i++) {
     const int a = sel[i];
     Work& w = ws[L.act[a]];
@@ -1062,6 +1064,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       // a sweep that moves at most this much weight in all ends the solve:
       // far below the 1e-5 target on f, and below a hundredth of the cutoff
       eps[i].move_tol = m->cfg.cutoff > 0 ? std::min(1e-10, 1e-2 * m->cfg.cutoff) : 1e-10;
+      eps[i].mv = d_mv + (size_t)i * maxh;
       eps[i].cut_lo = (int)m->h_res[16 * a + 6];
       eps[i].cut_hi = std::max(1, (int)m->h_res[16 * a + 7]);
     }
@@ -1100,6 +1103,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_mv, 0, sizeof(double) * n_mv, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_mode, 0, sizeof(int), m->stream));   // first sweep: the full chain
     CUDA_TRY(eig_prepare(f64));
     if (tc_apply) CUDA_TRY(eig_apply_tc_prepare());
@@ -1133,12 +1137,13 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     if (left) return not_converged(left, moved);
     return CTEBD_OK;
   }
-  std::vector<double> hoff(5 * na);   // counters, then the traces
+  std::vector<double> hoff(5 * na + n_mv);   // counters, the traces, the moved weights
   std::vector<double> last_moved(na, 0.0);
   std::vector<int> sweeps0(na);
   for (int i = 0; i < na; i++) sweeps0[i] = sweeps[sel[i]];
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_mv, 0, sizeof(double) * n_mv, m->stream));
     double fap_sweep = 0, bap_sweep = 0;
     for (int t = 0; t < max_nb - 1; t++) {
       double bin = 0;
@@ -1169,7 +1174,8 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
         }
       }
     }
-    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * 5 * na, cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(hoff.data(), d_off, sizeof(double) * (5 * na + n_mv), cudaMemcpyDeviceToHost,
+                             m->stream));
     CUDA_TRY(cudaStreamSynchronize(m->stream));
     bool any = false;
     double fap_done = 0;
@@ -1180,7 +1186,9 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       fap_done += hoff[4 * i + 2];
       if (!eps[i].active) continue;
       // same rules as the device-side loop's k_sweep_end
-      const double moved = hoff[4 * i + 3] / hoff[4 * na + i];
+      double mw = 0;   // summed in slot order, as on the device
+      for (int k = 0; k < eps[i].nb / 2; k++) mw += hoff[5 * na + (size_t)i * maxh + k];
+      const double moved = mw / hoff[4 * na + i];
       if (eps[i].cut_hi > 0 && eps[i].move_tol > 0 && sweeps[sel[i]] - sweeps0[i] >= 6 && moved > 0.9 * last_moved[i])
         eps[i].cut_hi = 0;
       last_moved[i] = moved;

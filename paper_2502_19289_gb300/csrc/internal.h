@@ -39,8 +39,7 @@ struct EigProb {
   int nb;       // number of JB-blocks, even
   int active;   // 0: converged, skip
   double* off;         // [0] significant rotations this sweep, [1] all rotations,
-                       // [2] flops of the tile updates actually applied (when jflag set),
-                       // [3] weight the significant rotations moved, sum |t g|
+                       // [2] flops of the tile updates actually applied (when jflag set)
   const double* scale; // trace of G (noise floor of the rotations)
   double floor_factor; // absolute rotation floor = eps * trace * floor_factor
   int* jflag;          // per pair slot: 1 when its J_p is not the identity; null: always apply
@@ -53,6 +52,8 @@ struct EigProb {
   void* T;             // npad x npad scratch of the tensor-core round update (FP32)
   double move_tol;     // > 0: the solve also ends after a sweep whose significant
                        // rotations moved at most move_tol * trace of weight in all
+  double* mv;          // move_tol > 0: per pair slot, the weight its significant
+                       // rotations moved this sweep (sum |t g|); summed in slot order
 };
 
 // Per-problem truncation inputs/outputs of one split level.

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   if (threadIdx.x == 0 && total > 0) {
     atomicAdd(P.off, (double)total_sig);
     atomicAdd(P.off + 1, (double)total);
-    atomicAdd(P.off + 3, last_move);   // of the block pair's last inner sweep
+    if (P.mv) P.mv[blockIdx.x] += last_move;   // of the block pair's last inner sweep; one writer per slot
   }
 }
 
@@ -817,7 +817,10 @@ __global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restri
     cum[4 * i] += P.off[1];
     cum[4 * i + 1] += P.off[2];
     cum[4 * i + 2] += 1.0;
-    const double moved = P.off[3] / (*P.scale), before = cum[4 * i + 3];
+    double mw = 0;   // the sweep's moved weight, summed in slot order
+    if (P.mv)
+      for (int k = 0; k < P.nb / 2; k++) { mw += P.mv[k]; P.mv[k] = 0.0; }
+    const double moved = mw / (*P.scale), before = cum[4 * i + 3];
     cum[4 * i + 3] = moved;   // weight the last sweep moved, relative to the trace
     // skipped rotations inside the cut's classes leave couplings that rotations
     // across the cut keep renewing: where the moved weight stalls, rotate every
@@ -825,7 +828,7 @@ __global__ void k_sweep_end(EigProb* __restrict__ probs, int n, double* __restri
     if (P.cut_hi > 0 && P.move_tol > 0 && cum[4 * i + 2] >= 6.0 && moved > 0.9 * before) P.cut_hi = 0;
     const bool settled = P.move_tol > 0 && moved <= P.move_tol;
     if (P.off[0] == 0.0 || settled) P.active = 0; else { any = true; n_active++; }
-    P.off[0] = 0.0; P.off[1] = 0.0; P.off[2] = 0.0; P.off[3] = 0.0;
+    P.off[0] = 0.0; P.off[1] = 0.0; P.off[2] = 0.0;
   }
   *n_sweeps += 1.0;
   if (compact) {

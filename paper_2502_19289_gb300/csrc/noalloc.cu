@@ -43,7 +43,8 @@ constexpr size_t NA_OFF_RHO = NA_OFF_J + al256((size_t)NA_N * 2 * NA_JB * NA_CPL
 constexpr size_t NA_OFF_PERM = NA_OFF_RHO + al256(2 * NA_N * sizeof(double));   // rho, then |v_i|^2
 constexpr size_t NA_OFF_RES = NA_OFF_PERM + al256(NA_N * sizeof(int));
 constexpr size_t NA_OFF_CNT = NA_OFF_RES + al256(8 * sizeof(double));
-constexpr size_t NA_OFF_DESC = NA_OFF_CNT + al256(5 * sizeof(double));
+constexpr int NA_SLOTS = NA_N / (2 * NA_JB);   // pair slots of the largest eigenproblem
+constexpr size_t NA_OFF_DESC = NA_OFF_CNT + al256((8 + NA_SLOTS) * sizeof(double));
 constexpr size_t NA_DESC_BYTES = 4096;
 constexpr size_t NA_BYTES = NA_OFF_DESC + NA_DESC_BYTES;   // ~2.4 MiB
 
@@ -115,8 +116,8 @@ static int na_gemm(NaDesc& d, const GemmProb& p) {
 static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor_factor,
                   double rel_skip, double move_rel, double move_tol) {
   // [0] significant rotations, [1] all rotations, [2] applied flops (the
-  // kernels' third counter, unused without pair flags), [3] weight moved by
-  // the significant rotations, [4] trace of G
+  // kernels' third counter, unused without pair flags), [4] trace of G,
+  // [8 ..) the weight moved by each pair slot's significant rotations
   double* cnt = (double*)(S + NA_OFF_CNT);
   EigProb e{};
   e.G = S + NA_OFF_G; e.V = acc; e.J = S + NA_OFF_J;
@@ -125,6 +126,7 @@ static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor
   e.rel_skip = rel_skip;   // no pair flags: every tile is updated
   e.move_rel = move_rel;
   e.move_tol = move_tol;
+  e.mv = move_tol > 0 ? cnt + 8 : nullptr;
   const EigProb* de;
   const size_t mark = d.off;
   if (int rc = d.put(&e, 1, &de)) return rc;
@@ -134,13 +136,15 @@ static int na_eig(NaDesc& d, unsigned char* S, void* acc, int npad, double floor
   bool converged = false;
   for (int sweep = 0; sweep < max_sweeps && !converged; sweep++) {
     NA_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(double), d.s));
+    NA_CUDA(cudaMemsetAsync(cnt + 8, 0, NA_SLOTS * sizeof(double), d.s));
     for (int t = 0; t < e.nb - 1; t++) {
       NA_CUDA(launch_eig_inner<float>(de, 1, e.nb, t, d.s));
       NA_CUDA(launch_eig_apply<float>(de, 1, e.nb, t, d.s));
     }
-    double h[5] = {0, 0, 0, 0, 0};
+    double h[8 + NA_SLOTS] = {};
     NA_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, d.s));
     NA_CUDA(cudaStreamSynchronize(d.s));
+    for (int k = 0; k < e.nb / 2; k++) h[3] += h[8 + k];   // moved weight, in slot order
     converged = h[0] == 0.0 || (move_tol > 0 && h[3] <= move_tol * h[4]);
     // a refinement pass still moving at most 1e-8 of the trace at the cap is
     // accepted, as on the handle path
