@@ -894,11 +894,13 @@ extern "C" int ctebd_set_sweep_graphs(int on) {
 // body holds two independent chains of round launches (joined before the
 // sweep-end kernel), so one half's latency-bound inner kernels can run while
 // the other half's apply kernels do.
-// Batches of more than kSweepCompact problems get a second chain of round
-// launches over a compact copy of the problems still active (grid y =
-// kSweepCompact): the last sweeps of a batch typically rotate one or two
-// problems, and the full grids' early-exiting CTAs then cost more than the work.
-constexpr int kSweepCompact = 8;
+// Batches of more than kSweepCompact problems at least kCompactMinBlocks
+// blocks wide get a second chain of round launches over a compact copy of the
+// problems still active (grid y = kSweepCompact): the last sweeps of such a
+// batch typically rotate one or two problems, and the full grids'
+// early-exiting CTAs then cost more than the work.  Narrower batches keep the
+// single chain: there the extra graph bodies cost more to build than the tail.
+constexpr int kSweepCompact = 8, kCompactMinBlocks = 32;
 
 static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector<int>& nbs, double* d_cum,
                            int max_sweeps, bool tc_apply, EigProb* d_compact, int* d_mode) {
@@ -913,7 +915,7 @@ static int run_sweep_graph(ctebd_mps* m, EigProb* dep, int na, const std::vector
   for (int i = 0; i < na; i++) (i < na0 ? nb0 : nb1) = std::max(i < na0 ? nb0 : nb1, nbs[i]);
   const int max_nb = std::max(nb0, nb1);
   const int JB = eig_block(f64);
-  const bool compact = na > kSweepCompact && d_compact && d_mode;
+  const bool compact = na > kSweepCompact && max_nb >= kCompactMinBlocks && d_compact && d_mode;
   auto chain = [&](EigProb* d, int n, int mnb, cudaStream_t s) -> cudaError_t {
     cudaError_t le = cudaSuccess;
     for (int t = 0; t < mnb - 1 && le == cudaSuccess; t++) {

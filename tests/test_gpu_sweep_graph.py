@@ -53,3 +53,35 @@ def test_switch_rejects_other_values():
     P = lib()
     import ctypes
     assert P._lib.ctebd_set_sweep_graphs(ctypes.c_int(2)) != 0
+
+
+
+def test_compact_tail_matches_host_sweeps():
+    """A batch of more than eight problems with some at least 32 blocks wide
+    runs its last sweeps on a compact chain (IF nodes in the device-side
+    loop).  One iteration of the chi_max = 1024 workload's circuit on 40
+    qubits saturated at chi = 512 (11 two-qubit clusters, 1024-wide splits):
+    both loops give the same ranks, sweep counts and fidelities, bit for bit."""
+    P = lib()
+    n, chi = 40, 512
+    w = synth.WORKLOADS[4]
+    c = synth.random_structured(n, w.n_layers, p1=w.p1, p2=w.p2, one_q=w.one_q,
+                                two_q=w.two_q, seed=4000)
+    circ = P.Circuit(n, c.gates, c.params)
+    chis, sites, lams = synth.random_right_canonical(n, chi, seed=4001, dtype=np.complex64)
+    cfg = P.make_config(n, chi, w.cutoff, w.k_max + 2 * 9, 0, w.k_max, P.FP32)
+    out = []
+    for graphs in (True, False):
+        P.set_sweep_graphs(graphs)
+        try:
+            mps = P.MPS(cfg)
+            mps.load(chis, sites, lams)
+            clusters, _, f = P.run_iteration(mps, circ, 0)
+            out.append((len(clusters), list(mps.bond_dims()), mps.split_log(), np.asarray(f)))
+        finally:
+            P.set_sweep_graphs(True)
+    (nc, chi_g, log_g, f_g), (_, chi_h, log_h, f_h) = out
+    assert nc > 8 and int(np.sum(log_g[:, 4] >= 1024)) > 0, (nc, log_g[:, 4].tolist())
+    assert chi_g == chi_h
+    np.testing.assert_array_equal(log_g[:, [5, 12, 13]], log_h[:, [5, 12, 13]])   # ranks, sweeps
+    np.testing.assert_array_equal(f_g, f_h)
