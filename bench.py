@@ -466,7 +466,7 @@ def run_apply_traffic(args):
     chis, sites, lams = synth.random_right_canonical(n, 1024, seed=4000, dtype=np.complex64)
     mps = P.MPS(cfg)
     mps.load(chis, sites, lams)
-    P.set_sweep_graphs(False)
+    P.set_sweep_graphs(0)
     clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, 0, mps.bond_dims(), cfg)
     Us = [P.cluster_unitary(circ.gates, circ.n_gates, cl) for cl in clusters]
     mps.step(clusters, Us)
@@ -570,9 +570,10 @@ def run_latency(args):
     of the library's kernels in a second, identical run with per-launch CUDA
     events.  Their ratio is the fraction of the step the GPU is busy; the rest
     is host work, launch gaps and the per-level reads, the most that capturing
-    a whole step into one graph could remove."""
-    import ctypes as C
-
+    a whole step into one graph could remove.  The first run takes the
+    default sweep-loop policy (device-side graphs for batches at least 16
+    blocks wide); two more drive every eigen-solve's sweep loop from the host,
+    then every one from a device-side graph."""
     import torch
 
     import paper_2502_19289_gb300 as P
@@ -605,12 +606,10 @@ def run_latency(args):
         out = {"steps": steps, "updates": upd, "step_wall_s": t_step, "max_chi": int(max(mps.bond_dims())),
                "logF": float(math.log(mps.fidelity()))}
         if profile:
-            rows = np.zeros(5 * 32)
-            nk = C.c_int(0)
-            P._check(P.lib.ctebd_profile_read(mps._h, rows.ctypes.data_as(C.POINTER(C.c_double)), 32,
-                                              C.byref(nk)), "ctebd_profile_read")
-            out["kernel_ms"] = float(sum(rows[5 * k + 1] for k in range(nk.value)))
-            out["launches"] = int(sum(rows[5 * k] for k in range(nk.value)))
+            cls = profile_rows(P, mps)
+            out["kernel_ms"] = float(sum(v["ms"] for v in cls.values()))
+            out["launches"] = int(sum(v["launches"] for v in cls.values()))
+            out["classes"] = cls
         mps.close()
         return out
 
@@ -621,15 +620,99 @@ def run_latency(args):
         run(w, base, False)   # warm-up
         plain = run(w, base, False)
         prof = run(w, base, True)
+        try:   # the same steps with every sweep loop driven from the host, then on the device
+            P.set_sweep_graphs(0)
+            host = run(w, base, False)
+            P.set_sweep_graphs(2)
+            dev = run(w, base, False)
+        finally:
+            P.set_sweep_graphs(1)
+        ns = max(prof["steps"], 1)
+        top = sorted(prof["classes"].items(), key=lambda kv: -kv[1]["ms"])[:5]
         res[name] = {"updates_per_s": plain["updates"] / plain["step_wall_s"], "steps": plain["steps"],
                      "step_ms": 1e3 * plain["step_wall_s"] / max(plain["steps"], 1),
-                     "kernel_ms_per_step": prof["kernel_ms"] / max(prof["steps"], 1),
-                     "launches_per_step": prof["launches"] / max(prof["steps"], 1),
+                     "step_ms_host_sweep_loop": 1e3 * host["step_wall_s"] / max(host["steps"], 1),
+                     "step_ms_device_sweep_loop": 1e3 * dev["step_wall_s"] / max(dev["steps"], 1),
+                     "kernel_ms_per_step": prof["kernel_ms"] / ns,
+                     "kernel_ms_per_step_by_class": {k: round(v["ms"] / ns, 4) for k, v in top},
+                     "launches_per_step": prof["launches"] / ns,
                      "gpu_busy_frac": prof["kernel_ms"] / 1e3 / plain["step_wall_s"],
                      "max_chi": plain["max_chi"]}
     print(json.dumps({"metric": "GPU-busy fraction of the step on latency-bound configurations",
                       "unit": "fraction", "n_gpus": 1, "data": "synthetic (seeded circuits from |0...0>)",
                       "configs": res}))
+
+
+def run_tebd(args):
+    """Cluster-TEBD against standard TEBD on the same circuits (Sec. IV.B,
+    Figs. 8-9).  Random-structured circuits from the paper's generator
+    (Sec. IV.A: every slot filled, a two-qubit gate with p = 0.5), with the
+    Clifford and the non-Clifford gate sets of App. A, run from |0...0>
+    through the whole circuit at one chi_max in the FP32 path.  Standard TEBD
+    is the special case of one layer per iteration and two-qubit clusters
+    (L_max = 1, k_max = 2).  Cluster-TEBD contracts as many layers per
+    iteration as its clusters allow under the memory bound (Eq. 7), with
+    Q_max = 3 + 2 log2 chi_max: the paper's runs at chi_max = 4096 used
+    Q_max = 27, the same three qubits of headroom between two saturated
+    bonds.  Clusters are also capped at k_max qubits (default 8), because
+    every cluster unitary is built as a dense 2^k x 2^k matrix.  Per
+    circuit: the wall time of each whole run (host partition and cluster
+    unitaries included), their ratio, and each run's fidelity product."""
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    import synth
+    chi, k_max, cut = args.chi, args.kmax, 1e-8
+    lg = int(math.log2(chi))
+    stream = torch.cuda.Stream()
+
+    def run(c, cluster):
+        n = c.n_qubits
+        cfg = (P.make_config(n, chi, cut, 3 + 2 * lg, 0, k_max, P.FP32) if cluster else
+               P.make_config(n, chi, cut, 2 + 2 * lg, 1, 2, P.FP32))
+        circ = P.Circuit(n, c.gates, c.params)
+        counts = [0, 0]
+
+        def count(s, e, cl, f):
+            counts[0] += 1
+            counts[1] += len(cl)
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mps = P.simulate(circ, cfg, stream.cuda_stream, callback=count)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+        out = {"s": wall, "F": float(mps.fidelity()), "iterations": counts[0], "updates": counts[1],
+               "max_chi": int(max(mps.bond_dims())), "layers": circ.n_layers}
+        mps.close()
+        return out
+
+    warm = synth.paper_random_structured(12, 10, clifford=False, seed=1)
+    run(warm, True)    # untimed: first launches, graph and kernel setup
+    run(warm, False)
+    rows = []
+    for clifford in (True, False):
+        for n, layers in ((40, 40), (40, 80), (100, 40), (100, 80)):
+            c = synth.paper_random_structured(n, layers, clifford=clifford,
+                                              seed=9000 + n + layers + (0 if clifford else 500))
+            t = run(c, False)
+            ct = run(c, True)
+            rows.append({"gates": "Clifford" if clifford else "non-Clifford", "n": n, "layers": t["layers"],
+                         "tebd_s": t["s"], "ctebd_s": ct["s"], "speedup": t["s"] / ct["s"],
+                         "F_tebd": t["F"], "F_ctebd": ct["F"], "iterations": [t["iterations"], ct["iterations"]],
+                         "updates": [t["updates"], ct["updates"]], "max_chi": [t["max_chi"], ct["max_chi"]]})
+    summary = {g: {"min": min(r["speedup"] for r in rows if r["gates"] == g),
+                   "max": max(r["speedup"] for r in rows if r["gates"] == g)}
+               for g in ("Clifford", "non-Clifford")}
+    print(json.dumps({"metric": "cluster-TEBD speed-up over standard TEBD (wall-time ratio, same circuit)",
+                      "unit": "x", "higher_is_better": True, "n_gpus": 1, "dtype": "c64",
+                      "data": "synthetic (the paper's random-structured generator, seeded; from |0...0>)",
+                      "config": {"workload": f"paper generator, Clifford and non-Clifford sets, n in (40, 100), "
+                                             f"40 and 80 layers, chi_max={chi}, cutoff 1e-8; cluster-TEBD "
+                                             f"k_max={k_max}, Q_max={3 + 2 * lg}; standard TEBD L_max=1, "
+                                             "k_max=2",
+                                 "timing": "wall clock of each whole simulation"},
+                      "speedup": summary, "circuits": rows}))
 
 
 def aggregate(dev_s: float, wall_s: float, units: int, device=None):
@@ -969,18 +1052,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=None,
                     help="qubits (default: 500 for cfg4, 60 for compare, 24 for apply-traffic, 100 for sketch-cfg4)")
-    ap.add_argument("--chi", type=int, default=1024)
-    ap.add_argument("--kmax", type=int, default=4,
-                    help="largest cluster (Q_max = kmax + 2 log2 chi); 6 lets k = 3..6 clusters form")
+    ap.add_argument("--chi", type=int, default=None, help="chi_max (default: 256 for tebd, else 1024)")
+    ap.add_argument("--kmax", type=int, default=None,
+                    help="largest cluster (default 8 for tebd, with Q_max = 3 + 2 log2 chi; else 4, "
+                         "with Q_max = kmax + 2 log2 chi: 6 lets k = 3..6 clusters form)")
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "cfg5", "compare", "apply-traffic", "latency"],
+    ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "cfg5", "compare", "apply-traffic", "latency",
+                             "tebd"],
                     help="cfg4: the headline (saturated chi=1024, full split); cfg2, sketch-cfg4: full vs "
                          "sketched split (cfg2, and cfg4's growing phase); "
                          "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations; "
                          "apply-traffic: small case for the round update's DRAM traffic; latency: GPU-busy "
                          "fraction of the step on small configurations; cfg5: packed circuits, each "
-                         "checked against its FP64-mode run")
+                         "checked against its FP64-mode run; tebd: cluster-TEBD against standard "
+                         "TEBD on the paper's generator")
     ap.add_argument("--circuits", type=int, default=64, help="cfg5: number of packed circuits")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="tensor-core policy (default 1, the size policy; 0 never; 2 always, "
@@ -990,6 +1076,13 @@ def main():
     args = ap.parse_args()
     if args.n is None:
         args.n = {"compare": 60, "apply-traffic": 24, "sketch-cfg4": 100}.get(args.workload, 500)
+    if args.chi is None:
+        args.chi = 256 if args.workload == "tebd" else 1024
+    if args.kmax is None:
+        args.kmax = 8 if args.workload == "tebd" else 4
+    if args.workload == "tebd":
+        run_tebd(args)
+        return
     if args.workload in ("cfg2", "sketch-cfg4"):
         run_cfg2(args)
         return

@@ -300,12 +300,14 @@ int tc_cgemm(const void* A, const void* B, void* C, int M, int K, int N, void* s
 int ctebd_set_tensor_cores(int mode);
 
 /* Eigen-solve sweep loop on the device (not in the paper): with per-launch
-   profiling off, each batched eigen-solve runs as one CUDA graph whose WHILE
+   profiling off, a batched eigen-solve runs as one CUDA graph whose WHILE
    node repeats a sweep until every problem has converged (or the sweep cap), with
-   no host round trip per sweep.  on = 1 (default) uses it, 0 launches every
-   round from the host.  Process-wide; results are the same either way.
+   no host round trip per sweep.  mode = 1 (default) uses it for batches at
+   least 16 Jacobi blocks wide (512 columns in FP32, 256 in FP64) and launches
+   the sweeps of narrower batches from the host; 2 uses it for every batch, 0
+   for none.  Process-wide; results are the same either way.
    Returns CTEBD_ERR_ARG for other values. */
-int ctebd_set_sweep_graphs(int on);
+int ctebd_set_sweep_graphs(int mode);
 
 /* Sweep cap of the Jacobi eigen-solves of the split (not in the paper; the
    solver of this implementation), process-wide, 1..1000 (default 60: the

@@ -205,10 +205,12 @@ def set_tensor_cores(mode: int):
     _check(_lib.ctebd_set_tensor_cores(int(mode)), "ctebd_set_tensor_cores")
 
 
-def set_sweep_graphs(on: bool):
-    """Run each eigen-solve's sweep loop on the device as one CUDA graph (default)
-    or launch every round from the host; process-wide (ctebd_set_sweep_graphs)."""
-    _check(_lib.ctebd_set_sweep_graphs(int(bool(on))), "ctebd_set_sweep_graphs")
+def set_sweep_graphs(mode: int):
+    """Where an eigen-solve's sweep loop runs: 1 (default) on the device as one
+    CUDA graph for batches at least 16 Jacobi blocks wide, from the host for
+    narrower ones; 2 on the device for every batch; 0 from the host for every
+    batch.  Process-wide (ctebd_set_sweep_graphs)."""
+    _check(_lib.ctebd_set_sweep_graphs(int(mode)), "ctebd_set_sweep_graphs")
 
 
 def set_max_sweeps(n: int):

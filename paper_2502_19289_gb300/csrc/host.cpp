@@ -867,9 +867,13 @@ static int level_gram(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const
 // sweep-end kernel, which folds the counters, retires converged problems and
 // sets the loop condition.  One launch and one host read per eigen-solve
 // instead of a host round trip per sweep.  Used when per-launch profiling is
-// off (ctebd_set_sweep_graphs; process-wide).
+// off, by default for batches at least kGraphMinBlocks blocks wide
+// (ctebd_set_sweep_graphs; process-wide): a narrower batch converges in a few
+// short sweeps, and building and instantiating its graph costs more than the
+// host round trips it saves.
 // ---------------------------------------------------------------------------
-static int g_sweep_graphs = 1;
+static int g_sweep_graphs = 1;   // 0 never, 1 wide batches, 2 always
+constexpr int kGraphMinBlocks = 16;
 static int g_max_sweeps = 60;
 
 namespace ctebd {
@@ -884,9 +888,9 @@ extern "C" int ctebd_set_max_sweeps(int n) {
 
 extern "C" int ctebd_max_sweeps(void) { return g_max_sweeps; }
 
-extern "C" int ctebd_set_sweep_graphs(int on) {
-  if (on < 0 || on > 1) return fail(CTEBD_ERR_ARG, "ctebd_set_sweep_graphs: 0 or 1");
-  g_sweep_graphs = on;
+extern "C" int ctebd_set_sweep_graphs(int mode) {
+  if (mode < 0 || mode > 2) return fail(CTEBD_ERR_ARG, "ctebd_set_sweep_graphs: 0, 1 or 2");
+  g_sweep_graphs = mode;
   return CTEBD_OK;
 }
 
@@ -1053,7 +1057,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     const int a = sel[i];
     Work& w = ws[L.act[a]];
     eps[i].G = w.G; eps[i].V = acc[i]; eps[i].J = w.J;
-    eps[i].npad = L.nepad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1;
+    eps[i].npad = L.nepad[a]; eps[i].nb = L.nbv[a]; eps[i].active = 1; eps[i].nact = L.ne[a];
     eps[i].off = d_off + 4 * i;
     eps[i].scale = d_off + 4 * na + i;
     eps[i].floor_factor = floor_factor;
@@ -1101,7 +1105,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
                                        std::to_string(na) + " problems still rotating after " +
                                        std::to_string(max_sweeps) + " sweeps" + tail);
   };
-  if (g_sweep_graphs && !m->prof.on) {
+  if (!m->prof.on && (g_sweep_graphs == 2 || (g_sweep_graphs == 1 && max_nb >= kGraphMinBlocks))) {
     // cumulative counters (rotations, applied flops, sweeps per problem) + sweep count
     CUDA_TRY(cudaMemsetAsync(d_cum, 0, sizeof(double) * n_cum, m->stream));
     CUDA_TRY(cudaMemsetAsync(d_off, 0, sizeof(double) * 4 * na, m->stream));
@@ -1123,7 +1127,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
     TRY(rc);
     // launches: every sweep runs both halves' rounds (counted as for one batch)
     const double rounds = hc[4 * na] * (max_nb - 1);
-    m->prof.launches[KK_EIG_INNER] += rounds;
+    m->prof.launches[KK_EIG_INNER] += hc[4 * na] * (max_nb > 2 ? max_nb : 1);   // + the one-pair launch
     m->prof.launches[KK_EIG_APPLY] += rounds * (tc_apply ? 2 : 1);
     if (tc_apply) m->prof.tc[KK_EIG_APPLY] += rounds * 2;
     for (int i = 0; i < na; i++) {
@@ -1160,6 +1164,7 @@ static int level_eig(ctebd_mps* m, std::vector<Work>& ws, const Level& L, const 
       }
       {
         ProfScope ps(m->prof, m->stream, KK_EIG_INNER, 0, bin);
+        m->prof.launches[KK_EIG_INNER] += eig_inner_launches(max_nb, t) - 1;
         CUDA_TRY(f64 ? launch_eig_inner<double>(dep, na, max_nb, t, m->stream)
                      : launch_eig_inner<float>(dep, na, max_nb, t, m->stream));
       }

@@ -54,6 +54,9 @@ struct EigProb {
                        // rotations moved at most move_tol * trace of weight in all
   double* mv;          // move_tol > 0: per pair slot, the weight its significant
                        // rotations moved this sweep (sum |t g|); summed in slot order
+  int nact;            // > 0: the eigen-dimension (rows / columns past it are zero); a
+                       // problem of one block pair then pairs only its first nact
+                       // (rounded up to even) indices; 0: all 2 JB
 };
 
 // Per-problem truncation inputs/outputs of one split level.
@@ -144,6 +147,8 @@ long long gemm_tiles(const GemmProb& p, bool fp64);
 
 template <typename R>
 cudaError_t launch_eig_init(const EigProb* d_probs, int n_probs, int max_npad, cudaStream_t s);
+// kernel launches of one launch_eig_inner call (round `round` of a batch of width max_nb)
+int eig_inner_launches(int max_nb, int round);
 template <typename R>
 cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, int round,
                              cudaStream_t s);

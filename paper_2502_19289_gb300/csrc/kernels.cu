@@ -190,8 +190,8 @@ __device__ __forceinline__ void jrot_params(R a, R d, typename C2<R>::T g, R flo
   ph.y = -g.y / ag;  // e^{-i phi}
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict__ probs, int round) {
+template <typename R, bool ONE_PAIR>
+__global__ void __launch_bounds__(256, ONE_PAIR ? 2 : 3) k_eig_inner(const EigProb* __restrict__ probs, int round) {
   using CT = typename C2<R>::T;
   constexpr int JB = EigCfg<R>::JB, D = 2 * JB, LD = D + 1, NBLK = JB * (JB + 1) / 2;
   // per thread: A blocks; Q rows row0 + j QSTEP (one rotation per thread)
@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   constexpr unsigned PMASK = JB == 32 ? 0xffffffffu : ((1u << JB) - 1u);   // lanes of the parameter phase
   static_assert(256 % JB == 0 && D % QSTEP == 0, "inner kernel: 256 threads");
   const EigProb P = probs[blockIdx.y];
-  if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2) return;
+  // each problem takes one variant whatever else shares the launch
+  if (!P.active || round >= P.nb - 1 || (int)blockIdx.x >= P.nb / 2 || ONE_PAIR != (P.nb == 2)) return;
   extern __shared__ unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
   CT* Q = A + D * LD;
@@ -239,6 +240,13 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   const R rel_skip = P.rel_skip > 0 ? (R)P.rel_skip : (R)4;
   const R move_abs = (R)(P.move_rel * (*P.scale));
   const bool track_move = P.move_tol > 0;   // the solve's moved-weight stopping rule
+  // ONE_PAIR (problems of one block pair, the whole matrix): past the
+  // eigen-dimension every row and column is zero and every rotation there is
+  // skipped, so the problem pairs only its first DE indices (DE - 1 rounds
+  // per sweep instead of D - 1).  The other pair slots hold identity
+  // rotations on disjoint padded pairs, and the blocks and Q columns they
+  // touch are left as they are.
+  const int DE = (ONE_PAIR && P.nact > 0) ? min(D, max(2, (P.nact + 1) & ~1)) : D, DH = DE / 2;
   __syncthreads();
   int total = 0, total_sig = 0;
   const int max_sweeps = P.nb == 2 ? EigCfg<R>::MAXS : 1;
@@ -246,9 +254,15 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   auto params = [&](int r) {
     if (threadIdx.x < JB) {
       int p, q;
-      circle(r, threadIdx.x, D, p, q);
       R c, s; CT e; bool skip, sig;
-      jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip, sig);
+      if (!ONE_PAIR || (int)threadIdx.x < DH) {
+        circle(r, threadIdx.x, DE, p, q);
+        jrot_params<R>(A[p * LD + p].x, A[q * LD + q].x, A[p * LD + q], floor_abs, rel_skip, c, s, e, skip, sig);
+      } else {
+        p = DE + 2 * ((int)threadIdx.x - DH);
+        q = p + 1;
+        skip = true; sig = false; c = 1; s = 0; e = cmk<CT>(1, 0);
+      }
       R mv = 0;   // the weight the rotation moves between p and q, |t g| (t = s / c)
       if (sig && move_abs > 0) {
         const CT g = A[p * LD + q];
@@ -282,7 +296,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     if (threadIdx.x == 0) { nrot = 0; nsig = 0; nmove = 0; }
     __syncthreads();
-    for (int r = 0; r < D - 1; r++) {
+    for (int r = 0; r < DE - 1; r++) {
       params(r);
       __syncthreads();
       // A <- R^H A R and Q <- Q R, every rotation in Rutishauser's form
@@ -294,31 +308,34 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
       // block below the diagonal is its conjugate transpose (A stays Hermitian).
       // Every element a thread touches in a round is its own, so all of its
       // loads (A blocks, Q pairs) are issued before any arithmetic or store.
-      int ia[NB_T], ib[NB_T];
+      int bab[NB_T];   // pair slots of the thread's blocks, a | b << 8 (a <= b)
       CT x00[NB_T], x10[NB_T], x01[NB_T], x11[NB_T];
 #pragma unroll
       for (int u = 0; u < NB_T; u++) {
         const int e = threadIdx.x + 256 * u;
-        const int bb = e < NBLK ? blk[e] : 0;
-        ia[u] = bb & 0xff;
-        ib[u] = bb >> 8;
-        const int pa = pp[ia[u]], qa = pq[ia[u]], pb = pp[ib[u]], qb = pq[ib[u]];
+        bab[u] = e < NBLK ? blk[e] : 0;
+        const int a = bab[u] & 0xff, b = bab[u] >> 8;
+        if (ONE_PAIR && b >= DH) continue;   // an identity slot: the block stays as it is
+        const int pa = pp[a], qa = pq[a], pb = pp[b], qb = pq[b];
         x00[u] = A[pa * LD + pb]; x10[u] = A[qa * LD + pb];
         x01[u] = A[pa * LD + qb]; x11[u] = A[qa * LD + qb];
       }
       const int kq = threadIdx.x % JB, row0 = threadIdx.x / JB;
       const int cp = pp[kq], cq = pq[kq];
+      const bool qrot = !ONE_PAIR || kq < DH;
       CT xq[QROWS], yq[QROWS];
 #pragma unroll
       for (int j = 0; j < QROWS; j++) {
         const int row = row0 + j * QSTEP;
-        xq[j] = Q[row * LD + cp];
-        yq[j] = Q[row * LD + cq];
+        if (qrot) {
+          xq[j] = Q[row * LD + cp];
+          yq[j] = Q[row * LD + cq];
+        }
       }
 #pragma unroll
       for (int u = 0; u < NB_T; u++) {
-        if (threadIdx.x + 256 * u >= NBLK) continue;
-        const int a = ia[u], b = ib[u];
+        const int a = bab[u] & 0xff, b = bab[u] >> 8;
+        if (threadIdx.x + 256 * u >= NBLK || (ONE_PAIR && b >= DH)) continue;
         const int pa = pp[a], qa = pq[a], pb = pp[b], qb = pq[b];
         const R tb = tu[b], sb = sn[b];
         const CT fb = ph[b];
@@ -341,7 +358,7 @@ __global__ void __launch_bounds__(256, 3) k_eig_inner(const EigProb* __restrict_
           A[pb * LD + qa] = cconj(m10); A[qb * LD + qa] = cconj(m11);
         }
       }
-      {
+      if (qrot) {
         const R t = tu[kq], s = sn[kq];
         const CT f = ph[kq];
 #pragma unroll
@@ -752,7 +769,8 @@ static void eig_attrs() {
   const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
                           sizeof(unsigned short) * JB * (JB + 1) / 2;
   const size_t sm_apply = 2 * sizeof(CT) * D * LD;
-  cudaFuncSetAttribute(k_eig_inner<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
+  cudaFuncSetAttribute(k_eig_inner<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
+  cudaFuncSetAttribute(k_eig_inner<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_inner);
   cudaFuncSetAttribute(k_eig_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
   attr = true;
 }
@@ -764,9 +782,18 @@ cudaError_t launch_eig_inner(const EigProb* d_probs, int n_probs, int max_nb, in
   eig_attrs<R>();
   const size_t sm_inner = 2 * sizeof(CT) * D * LD + JB * (2 * sizeof(R) + sizeof(CT) + 2 * sizeof(int)) +
                           sizeof(unsigned short) * JB * (JB + 1) / 2;
-  k_eig_inner<R><<<dim3(max_nb / 2, n_probs), 256, sm_inner, s>>>(d_probs, round);
+  // problems of one block pair (nb == 2) have a single round, the first; the
+  // others run the general variant
+  if (max_nb > 2) {
+    k_eig_inner<R, false><<<dim3(max_nb / 2, n_probs), 256, sm_inner, s>>>(d_probs, round);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (round == 0) k_eig_inner<R, true><<<dim3(1, n_probs), 256, sm_inner, s>>>(d_probs, round);
   return cudaGetLastError();
 }
+
+int eig_inner_launches(int max_nb, int round) { return (max_nb > 2 ? 1 : 0) + (round == 0 ? 1 : 0); }
 
 template <typename R>
 cudaError_t launch_eig_apply(const EigProb* d_probs, int n_probs, int max_nb, int round, cudaStream_t s) {

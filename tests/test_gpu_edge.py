@@ -62,7 +62,7 @@ def test_sweep_cap_reports_numeric_error(graphs):
     cfg = P.make_config(12, 64, 1e-8, 2 + 12 + 2, 0, 2, P.FP32)
     cap = P.max_sweeps()
     try:
-        P.set_sweep_graphs(graphs)
+        P.set_sweep_graphs(2 if graphs else 0)
         P.set_max_sweeps(1)
         mps = P.MPS(cfg)
         mps.load(chis, sites, lams)
@@ -70,7 +70,7 @@ def test_sweep_cap_reports_numeric_error(graphs):
             mps.step([P.Cluster(5, 2, 0, 0)], [U])
     finally:
         P.set_max_sweeps(cap)
-        P.set_sweep_graphs(True)
+        P.set_sweep_graphs(1)
     mps = P.MPS(cfg)
     mps.load(chis, sites, lams)
     f = mps.step([P.Cluster(5, 2, 0, 0)], [U])

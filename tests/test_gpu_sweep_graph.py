@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _run(P, c, w, chi, graphs, precision):
-    P.set_sweep_graphs(graphs)
+    P.set_sweep_graphs(2 if graphs else 0)
     try:
         circ = P.Circuit(c.n_qubits, c.gates, c.params)
         cfg = P.make_config(c.n_qubits, chi, w.cutoff, w.q_max, 0, w.k_max, precision)
@@ -26,7 +26,7 @@ def _run(P, c, w, chi, graphs, precision):
             start = stop
         return mps, np.concatenate(logs)
     finally:
-        P.set_sweep_graphs(True)
+        P.set_sweep_graphs(1)
 
 
 @pytest.mark.parametrize("precision_name,chi", [("FP32", 32), ("FP32", 256), ("FP64", 32)])
@@ -52,7 +52,8 @@ def test_device_sweeps_match_host_sweeps(precision_name, chi):
 def test_switch_rejects_other_values():
     P = lib()
     import ctypes
-    assert P._lib.ctebd_set_sweep_graphs(ctypes.c_int(2)) != 0
+    assert P._lib.ctebd_set_sweep_graphs(ctypes.c_int(3)) != 0
+    assert P._lib.ctebd_set_sweep_graphs(ctypes.c_int(-1)) != 0
 
 
 
@@ -72,14 +73,14 @@ def test_compact_tail_matches_host_sweeps():
     cfg = P.make_config(n, chi, w.cutoff, w.k_max + 2 * 9, 0, w.k_max, P.FP32)
     out = []
     for graphs in (True, False):
-        P.set_sweep_graphs(graphs)
+        P.set_sweep_graphs(2 if graphs else 0)
         try:
             mps = P.MPS(cfg)
             mps.load(chis, sites, lams)
             clusters, _, f = P.run_iteration(mps, circ, 0)
             out.append((len(clusters), list(mps.bond_dims()), mps.split_log(), np.asarray(f)))
         finally:
-            P.set_sweep_graphs(True)
+            P.set_sweep_graphs(1)
     (nc, chi_g, log_g, f_g), (_, chi_h, log_h, f_h) = out
     assert nc > 8 and int(np.sum(log_g[:, 4] >= 1024)) > 0, (nc, log_g[:, 4].tolist())
     assert chi_g == chi_h
