@@ -715,6 +715,87 @@ def run_tebd(args):
                       "speedup": summary, "circuits": rows}))
 
 
+def run_shor(args):
+    """Cluster-TEBD against standard TEBD on Shor's order-finding circuit
+    (Sec. IV.B, Fig. 10): Beauregard's construction for N with base a, t
+    counting qubits (default: the phase-estimation size for the precision the
+    paper used for that N), every long-range gate routed through
+    nearest-neighbour SWAPs.  Both modes run from |0...0> through the whole
+    circuit in the FP32 path; standard TEBD is L_max = 1, k_max = 2, and
+    cluster-TEBD takes Q_max = 3 + 2 log2 chi_max with clusters of at most
+    k_max qubits (default 8).  For t <= 10 and at most 24 qubits, the counting
+    register's distribution from each final state is compared with its closed
+    form, sum_z |2^-t sum_{C : a^C = z mod N} exp(-2 pi i y C / 2^t)|^2."""
+    import torch
+
+    import paper_2502_19289_gb300 as P
+    from synth.shor import counting_qubits, shor_circuit
+    eps = {15: 1e-3, 21: 1e-4, 35: 1e-5, 91: 1e-5, 221: 1e-9}
+    N, a = args.shor_n, args.shor_a
+    t = args.shor_t if args.shor_t > 0 else counting_qubits(N, eps.get(N, 1e-3))
+    chi, k_max, cut = args.chi, args.kmax, 1e-8
+    lg = int(math.log2(chi))
+    c = shor_circuit(N, a, t)
+    n = c.n_qubits
+    circ = P.Circuit(n, c.gates, c.params)
+    stream = torch.cuda.Stream()
+
+    def run(circuit, nq, cluster):
+        cfg = (P.make_config(nq, chi, cut, 3 + 2 * lg, 0, k_max, P.FP32) if cluster else
+               P.make_config(nq, chi, cut, 2 + 2 * lg, 1, 2, P.FP32))
+        counts = [0, 0]
+
+        def count(s, e, cl, f):
+            counts[0] += 1
+            counts[1] += len(cl)
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mps = P.simulate(circuit, cfg, stream.cuda_stream, callback=count)
+        stream.synchronize()
+        return mps, {"s": time.perf_counter() - t0, "F": float(mps.fidelity()), "iterations": counts[0],
+                     "updates": counts[1], "max_chi": int(max(mps.bond_dims()))}
+
+    def counting_error(mps):
+        if t > 10 or n > 24:
+            return None
+        v = np.ones((1, 1), dtype=np.complex128)
+        for q in range(n):
+            s = mps.site(q)
+            v = np.einsum("ia,asb->isb", v, s).reshape(-1, s.shape[2])
+        p = np.abs(v.reshape((2,) * n)) ** 2
+        pc = p.sum(axis=tuple(range(t, n)))
+        got = np.zeros(1 << t)
+        for idx in np.ndindex(*(2,) * t):
+            got[sum(idx[t - 1 - k] << k for k in range(t))] += pc[idx]
+        C = np.arange(1 << t)
+        z = np.array([pow(a, int(k), N) for k in C])
+        ref = np.array([sum(abs(np.exp(-2j * np.pi * y * C[z == u] / (1 << t)).sum() / (1 << t)) ** 2
+                            for u in np.unique(z)) for y in range(1 << t)])
+        return float(np.max(np.abs(got / got.sum() - ref)))
+
+    warm = shor_circuit(15, 2, 1)
+    for cl in (True, False):   # untimed: first launches, graph and kernel setup
+        m, _ = run(P.Circuit(warm.n_qubits, warm.gates, warm.params), warm.n_qubits, cl)
+        m.close()
+    out = {}
+    for name, cl in (("tebd", False), ("cluster_tebd", True)):
+        m, r = run(circ, n, cl)
+        r["counting_register_max_abs_error"] = counting_error(m)
+        m.close()
+        out[name] = r
+    print(json.dumps({"metric": "cluster-TEBD speed-up over standard TEBD on Shor's circuit (wall-time ratio)",
+                      "value": out["tebd"]["s"] / out["cluster_tebd"]["s"], "unit": "x",
+                      "higher_is_better": True, "n_gpus": 1, "dtype": "c64",
+                      "data": "synthetic (Beauregard's order-finding circuit, SWAP-routed; from |0...0>)",
+                      "config": {"workload": f"Shor order finding N={N}, a={a}, t={t} counting qubits, {n} qubits, "
+                                             f"{circ.n_gates} gates in {circ.n_layers} layers; chi_max={chi}, cutoff "
+                                             f"1e-8; cluster-TEBD k_max={k_max}, Q_max={3 + 2 * lg}; standard TEBD "
+                                             "L_max=1, k_max=2",
+                                 "timing": "wall clock of each whole simulation"},
+                      "qubits": n, "gates": circ.n_gates, "layers": circ.n_layers, "arms": out}))
+
+
 def aggregate(dev_s: float, wall_s: float, units: int, device=None):
     """Whole-job figures over all ranks: max of the times, sum of the units.
 
@@ -1059,15 +1140,19 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="cfg4", choices=["cfg4", "cfg2", "sketch-cfg4", "cfg5", "compare", "apply-traffic", "latency",
-                             "tebd"],
+                             "tebd", "shor"],
                     help="cfg4: the headline (saturated chi=1024, full split); cfg2, sketch-cfg4: full vs "
                          "sketched split (cfg2, and cfg4's growing phase); "
                          "compare: FP32 path, FP64 mode and the plain FP64 path over the same iterations; "
                          "apply-traffic: small case for the round update's DRAM traffic; latency: GPU-busy "
                          "fraction of the step on small configurations; cfg5: packed circuits, each "
                          "checked against its FP64-mode run; tebd: cluster-TEBD against standard "
-                         "TEBD on the paper's generator")
+                         "TEBD on the paper's generator; shor: the same on Shor's order-finding circuit")
     ap.add_argument("--circuits", type=int, default=64, help="cfg5: number of packed circuits")
+    ap.add_argument("--shor-n", type=int, default=15, help="shor: the number to factor")
+    ap.add_argument("--shor-a", type=int, default=2, help="shor: the base (coprime with N)")
+    ap.add_argument("--shor-t", type=int, default=0,
+                    help="shor: counting qubits (default: phase-estimation size for the paper's precision)")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="tensor-core policy (default 1, the size policy; 0 never; 2 always, "
                          "including the Jacobi round updates)")
@@ -1077,11 +1162,14 @@ def main():
     if args.n is None:
         args.n = {"compare": 60, "apply-traffic": 24, "sketch-cfg4": 100}.get(args.workload, 500)
     if args.chi is None:
-        args.chi = 256 if args.workload == "tebd" else 1024
+        args.chi = {"tebd": 256, "shor": 256}.get(args.workload, 1024)
     if args.kmax is None:
-        args.kmax = 8 if args.workload == "tebd" else 4
+        args.kmax = 8 if args.workload in ("tebd", "shor") else 4
     if args.workload == "tebd":
         run_tebd(args)
+        return
+    if args.workload == "shor":
+        run_shor(args)
         return
     if args.workload in ("cfg2", "sketch-cfg4"):
         run_cfg2(args)
