@@ -184,28 +184,77 @@ extern "C" int cluster_partition(const ctebd_gate* gates, int n_gates, int layer
   return CTEBD_OK;
 }
 
-// apply a gate to a k-qubit state vector (local qubits, MSB = position 0)
-static void gate_on_vec(int k, cd* v, int gnq, const int* lq, const cd* g) {
+// M <- G M for a gate on window qubits lq of a row-major 2^k x 2^k matrix:
+// the gate mixes whole rows (the row index is big-endian over the window: the
+// window's first qubit is the most significant bit, and bit t of a gate's
+// own index belongs to its qubit lq[gnq - 1 - t]), so each update streams
+// contiguous rows.  A gate whose
+// matrix is a permutation (X, CNOT, SWAP) moves rows, a diagonal one scales
+// them (rows with factor 1 are skipped), any other one takes the full sums.
+// Complex products are written out in real arithmetic.
+static void gate_on_rows(int k, cd* M, int gnq, const int* lq, const cd* g, std::vector<cd>& tmp) {
+  const long long D = 1LL << k;
   const int dim = 1 << gnq;
   long long mask = 0;
   int pos[3];
   for (int t = 0; t < gnq; t++) { pos[t] = k - 1 - lq[t]; mask |= 1LL << pos[t]; }
-  cd in[8], outv[8];
-  long long idx[8];
-  for (long long base = 0; base < (1LL << k); base++) {
+  bool diag = true, perm = true;
+  int src[8];
+  for (int a = 0; a < dim; a++) {
+    int ones = 0;
+    src[a] = -1;
+    for (int c = 0; c < dim; c++) {
+      const cd v = g[a * dim + c];
+      if (a != c && v != cd(0.0)) diag = false;
+      if (v == cd(1.0)) { ones++; src[a] = c; }
+      else if (v != cd(0.0)) perm = false;
+    }
+    if (ones != 1) perm = false;
+  }
+  if ((long long)tmp.size() < dim * D) tmp.resize(dim * D);
+  double* row[8];
+  for (long long base = 0; base < D; base++) {
     if (base & mask) continue;
     for (int x = 0; x < dim; x++) {
       long long i = base;
       for (int t = 0; t < gnq; t++) if ((x >> (gnq - 1 - t)) & 1) i |= 1LL << pos[t];
-      idx[x] = i;
-      in[x] = v[i];
+      row[x] = reinterpret_cast<double*>(M + i * D);
     }
-    for (int a = 0; a < dim; a++) {
-      cd s = 0;
-      for (int c = 0; c < dim; c++) s += g[a * dim + c] * in[c];
-      outv[a] = s;
+    if (diag) {
+      for (int a = 0; a < dim; a++) {
+        const double gr = g[a * dim + a].real(), gi = g[a * dim + a].imag();
+        if (gr == 1.0 && gi == 0.0) continue;
+        double* r = row[a];
+        for (long long j = 0; j < D; j++) {
+          const double xr = r[2 * j], xi = r[2 * j + 1];
+          r[2 * j] = gr * xr - gi * xi;
+          r[2 * j + 1] = gr * xi + gi * xr;
+        }
+      }
+      continue;
     }
-    for (int x = 0; x < dim; x++) v[idx[x]] = outv[x];
+    if (perm) {
+      for (int a = 0; a < dim; a++)
+        if (src[a] != a) std::memcpy(tmp.data() + a * D, row[src[a]], sizeof(cd) * D);
+      for (int a = 0; a < dim; a++)
+        if (src[a] != a) std::memcpy(row[a], tmp.data() + a * D, sizeof(cd) * D);
+      continue;
+    }
+    double gr[64], gi[64];
+    for (int e = 0; e < dim * dim; e++) { gr[e] = g[e].real(); gi[e] = g[e].imag(); }
+    for (long long j = 0; j < D; j++) {
+      double xr[8], xi[8];
+      for (int c = 0; c < dim; c++) { xr[c] = row[c][2 * j]; xi[c] = row[c][2 * j + 1]; }
+      for (int a = 0; a < dim; a++) {
+        double sr = 0, si = 0;
+        for (int c = 0; c < dim; c++) {
+          sr += gr[a * dim + c] * xr[c] - gi[a * dim + c] * xi[c];
+          si += gr[a * dim + c] * xi[c] + gi[a * dim + c] * xr[c];
+        }
+        row[a][2 * j] = sr;
+        row[a][2 * j + 1] = si;
+      }
+    }
   }
 }
 
@@ -213,7 +262,7 @@ extern "C" int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd
   if (!c || !U || c->k < 1 || c->k > 12) return fail(CTEBD_ERR_ARG, "cluster_unitary: bad args");
   const int k = c->k;
   const long long D = 1LL << k;
-  std::vector<cd> M(D * D, 0.0), col(D);
+  std::vector<cd> M(D * D, 0.0), tmp;
   for (long long i = 0; i < D; i++) M[i * D + i] = 1;
   std::vector<int> order;
   for (int i = 0; i < n_gates; i++)
@@ -231,11 +280,7 @@ extern "C" int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd
     cd gm[16];
     const int d = gate_dim(g.kind, g.param, gm);
     if (!d || (d == 2) != (g.n_q == 1)) return fail(CTEBD_ERR_ARG, "cluster_unitary: unknown gate kind");
-    for (long long cI = 0; cI < D; cI++) {
-      for (long long r = 0; r < D; r++) col[r] = M[r * D + cI];
-      gate_on_vec(k, col.data(), g.n_q, lq, gm);
-      for (long long r = 0; r < D; r++) M[r * D + cI] = col[r];
-    }
+    gate_on_rows(k, M.data(), g.n_q, lq, gm, tmp);
   }
   for (long long i = 0; i < D * D; i++) { U[2 * i] = M[i].real(); U[2 * i + 1] = M[i].imag(); }
   return CTEBD_OK;
