@@ -121,3 +121,32 @@ def test_cluster_unitary_matches_oracle(seed):
         U = P.cluster_unitary(circ.gates, circ.n_gates, cl)
         Uo = oracle.cluster_unitary(cl.q0, cl.k, c, lo, 0, stop)
         np.testing.assert_allclose(U, Uo, atol=1e-14)
+
+
+@pytest.mark.parametrize("source", ["paper-nonclifford", "shor"])
+def test_cluster_unitary_all_gate_kinds(source):
+    """Cluster unitaries of 6 to 10 qubits over every gate kind: permutation
+    gates (X, CNOT, SWAP), diagonal ones (Z, S, T, P, CZ, CS, CT, CP) and dense
+    ones (H, Y, X^1/4, sqrt W, CY, CH, sqrt SWAP), against the oracle's product
+    and against unitarity."""
+    if source == "shor":
+        from synth.shor import shor_circuit
+        c = shor_circuit(15, 7, 2)
+    else:
+        c = synth.paper_random_structured(14, 12, clifford=False, seed=21)
+    n = c.n_qubits
+    circ, lo, nlo, _ = _layers_both(c)
+    kmax = 8 if source == "shor" else 10
+    cfg = P.make_config(n, 1, 0.0, kmax, 0, kmax)
+    start, seen, kseen = 0, 0, 0
+    while start < circ.n_layers and seen < 16:
+        clusters, stop = P.cluster_partition(circ.gates, circ.n_gates, start, np.ones(n + 1), cfg)
+        for cl in clusters:
+            U = P.cluster_unitary(circ.gates, circ.n_gates, cl)
+            Uo = oracle.cluster_unitary(cl.q0, cl.k, c, lo, start, stop)
+            np.testing.assert_allclose(U, Uo, atol=1e-13)
+            np.testing.assert_allclose(U @ U.conj().T, np.eye(U.shape[0]), atol=1e-12)
+            seen += 1
+            kseen = max(kseen, cl.k)
+        start = stop
+    assert kseen >= 6
