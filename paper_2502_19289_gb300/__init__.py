@@ -434,13 +434,32 @@ def amplitude(mps: MPS, bits) -> complex:
     return mps.amplitude(bits)
 
 
+def _by_layer(gates, n_gates):
+    """A copy of a layered gate array in layer order (stable: the given order
+    within a layer).  The partition, the cluster unitaries and the one-qubit
+    pass find a layer range in such an array by binary search instead of
+    sorting the whole list on every call; their results are the same."""
+    out = (Gate * max(n_gates, 1))()
+    if n_gates:
+        layer = np.array([gates[i].layer for i in range(n_gates)], dtype=np.int64)
+        order = np.argsort(layer, kind="stable")
+        sz = C.sizeof(Gate)
+        src = np.frombuffer((C.c_char * (sz * n_gates)).from_address(C.addressof(gates)), dtype=np.uint8)
+        dst = np.frombuffer((C.c_char * (sz * n_gates)).from_address(C.addressof(out)), dtype=np.uint8)
+        dst[:] = src.reshape(n_gates, sz)[order].reshape(-1)
+    return out
+
+
 class Circuit:
-    """A circuit in the library's gate format, layered (Sec. II.A)."""
+    """A circuit in the library's gate format, layered (Sec. II.A).  ``gates``
+    keeps the given order; ``gates_by_layer`` holds the same gates in layer
+    order, which the iteration drivers pass to the library."""
 
     def __init__(self, n_qubits: int, gates5, params):
         self.n = n_qubits
         self.gates, self.n_gates = gates_from_arrays(gates5, params)
         self.n_layers = assign_layers(self.gates, self.n_gates, n_qubits)
+        self.gates_by_layer = _by_layer(self.gates, self.n_gates)
 
 
 def run_iteration(mps: MPS, circ: Circuit, start: int, hint_fn=None):
@@ -450,15 +469,16 @@ def run_iteration(mps: MPS, circ: Circuit, start: int, hint_fn=None):
     rank hints: ``hint_fn(clusters, chi)`` if given (the learned predictor,
     see ``rank_model.make_hint_fn``), else the Eq. 9 bound.  Returns (clusters, stop layer, per-split f)."""
     chi = mps.bond_dims()
-    clusters, stop = cluster_partition(circ.gates, circ.n_gates, start, chi, mps.cfg)
+    g = circ.gates_by_layer
+    clusters, stop = cluster_partition(g, circ.n_gates, start, chi, mps.cfg)
     if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32 and clusters:
         hints = (hint_fn(clusters, chi) if hint_fn else
-                 [cluster_rank_bounds(circ.gates, circ.n_gates, c, chi) for c in clusters])
+                 [cluster_rank_bounds(g, circ.n_gates, c, chi) for c in clusters])
         for c, hint in zip(clusters, hints):
             for j, h in enumerate(hint[:11]):
                 c.rank_hint[j] = int(h)
-    mps.apply_singletons(circ.gates, circ.n_gates, clusters, start, stop)
-    Us = [cluster_unitary(circ.gates, circ.n_gates, c) for c in clusters]
+    mps.apply_singletons(g, circ.n_gates, clusters, start, stop)
+    Us = [cluster_unitary(g, circ.n_gates, c) for c in clusters]
     f = mps.step(clusters, Us) if clusters else np.zeros(0)
     return clusters, stop, f
 
@@ -515,16 +535,17 @@ class PackedCircuits:
             if self.start[i] >= loc.n_layers:
                 continue
             cfg_local.n_qubits = loc.n
-            cl, stop = cluster_partition(loc.gates, loc.n_gates, self.start[i], chi[off:off + loc.n + 1],
-                                         cfg_local)
+            cl, stop = cluster_partition(loc.gates_by_layer, loc.n_gates, self.start[i],
+                                         chi[off:off + loc.n + 1], cfg_local)
             for c in cl:
                 c.q0 += off
-            mps.apply_singletons(glob.gates, glob.n_gates, cl, self.start[i], stop)
+            gg = glob.gates_by_layer
+            mps.apply_singletons(gg, glob.n_gates, cl, self.start[i], stop)
             if mps.cfg.sketch_oversample > 0 and mps.cfg.precision == FP32:
                 for c in cl:
-                    for j, h in enumerate(cluster_rank_bounds(glob.gates, glob.n_gates, c, chi)[:11]):
+                    for j, h in enumerate(cluster_rank_bounds(gg, glob.n_gates, c, chi)[:11]):
                         c.rank_hint[j] = int(h)
-            Us.extend(cluster_unitary(glob.gates, glob.n_gates, c) for c in cl)
+            Us.extend(cluster_unitary(gg, glob.n_gates, c) for c in cl)
             all_clusters.extend(cl)
             self.start[i] = stop
         if all_clusters:

@@ -130,6 +130,29 @@ static bool clusters_fit(const std::vector<char>& bond, int n, const int* chi, i
   return true;
 }
 
+// True when the gates are in non-decreasing layer order (then the gates of a
+// layer range are one contiguous run, found by binary search).
+static bool layer_sorted(const ctebd_gate* gates, int n_gates) {
+  for (int i = 1; i < n_gates; i++)
+    if (gates[i].layer < gates[i - 1].layer) return false;
+  return true;
+}
+
+// Indices of the gates in layers (lo, hi], in layer order and, within a
+// layer, in the given order.
+static void gates_in_layers(const ctebd_gate* gates, int n_gates, int lo, int hi, std::vector<int>& idx) {
+  idx.clear();
+  if (layer_sorted(gates, n_gates)) {
+    const ctebd_gate* b = std::lower_bound(gates, gates + n_gates, lo + 1,
+                                           [](const ctebd_gate& g, int L) { return g.layer < L; });
+    for (const ctebd_gate* g = b; g < gates + n_gates && g->layer <= hi; ++g) idx.push_back((int)(g - gates));
+    return;
+  }
+  for (int i = 0; i < n_gates; i++)
+    if (gates[i].layer > lo && gates[i].layer <= hi) idx.push_back(i);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+}
+
 extern "C" int cluster_partition(const ctebd_gate* gates, int n_gates, int layer_start, const int* chi,
                                  const ctebd_config* cfg, ctebd_cluster* out, int cap, int* n_out,
                                  int* layer_stop) {
@@ -138,14 +161,12 @@ extern "C" int cluster_partition(const ctebd_gate* gates, int n_gates, int layer
   const int n = cfg->n_qubits;
   int n_layers = 0;
   for (int i = 0; i < n_gates; i++) n_layers = std::max(n_layers, gates[i].layer);
-  // bucket gates by layer once
-  std::vector<int> order(n_gates);
-  for (int i = 0; i < n_gates; i++) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+  // the gates after layer_start in layer order
+  std::vector<int> order;
+  gates_in_layers(gates, n_gates, layer_start, n_layers, order);
   std::vector<char> bond(n + 1, 0), tent;
   int stop = layer_start;
-  size_t pos = std::lower_bound(order.begin(), order.end(), layer_start + 1,
-                                [&](int gi, int L) { return gates[gi].layer < L; }) - order.begin();
+  size_t pos = 0;
   for (int L = layer_start + 1; L <= n_layers; L++) {
     if (cfg->l_max > 0 && L - layer_start > cfg->l_max) break;
     tent = bond;
@@ -265,9 +286,7 @@ extern "C" int cluster_unitary(const ctebd_gate* gates, int n_gates, const ctebd
   std::vector<cd> M(D * D, 0.0), tmp;
   for (long long i = 0; i < D; i++) M[i * D + i] = 1;
   std::vector<int> order;
-  for (int i = 0; i < n_gates; i++)
-    if (gates[i].layer > c->layer_lo && gates[i].layer <= c->layer_hi) order.push_back(i);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gates[a].layer < gates[b].layer; });
+  gates_in_layers(gates, n_gates, c->layer_lo, c->layer_hi, order);
   for (int gi : order) {
     const ctebd_gate& g = gates[gi];
     int lq[3], inside = 0;
