@@ -150,3 +150,34 @@ def test_cluster_unitary_all_gate_kinds(source):
             kseen = max(kseen, cl.k)
         start = stop
     assert kseen >= 6
+
+
+@pytest.mark.parametrize("source", ["cfg2", "shor"])
+def test_layer_sorted_copy(source):
+    """Circuit.gates_by_layer holds the same gates in non-decreasing layer
+    order (the given order within a layer), and the partition and the
+    cluster unitaries it feeds are those of the given order."""
+    if source == "shor":
+        from synth.shor import shor_circuit
+        c = shor_circuit(15, 7, 2)
+    else:
+        c = synth.reduced(2, 24, 20).circuit(2, 2)
+    n = c.n_qubits
+    circ = P.Circuit(n, c.gates, c.params)
+    g0, g1 = circ.gates, circ.gates_by_layer
+    rows = lambda g, i: (g[i].layer, g[i].n_q, tuple(g[i].q), g[i].kind, g[i].param)
+    a = [rows(g0, i) for i in range(circ.n_gates)]
+    b = [rows(g1, i) for i in range(circ.n_gates)]
+    assert [x[0] for x in b] == sorted(x[0] for x in b)
+    assert b == sorted(a, key=lambda x: x[0])          # stable: Python's sort is stable
+    chis = np.minimum(np.asarray([2 ** min(q, n - q) for q in range(n + 1)], dtype=np.int32), 8)
+    for cfg in (P.make_config(n, 64, 1e-8, 8, 1, 2), P.make_config(n, 64, 1e-8, 12, 0, 6)):
+        start = 0
+        while start < circ.n_layers:
+            cl0, s0 = P.cluster_partition(g0, circ.n_gates, start, chis, cfg)
+            cl1, s1 = P.cluster_partition(g1, circ.n_gates, start, chis, cfg)
+            assert s0 == s1 and [(x.q0, x.k) for x in cl0] == [(x.q0, x.k) for x in cl1]
+            for x, y in zip(cl0, cl1):
+                np.testing.assert_array_equal(P.cluster_unitary(g0, circ.n_gates, x),
+                                              P.cluster_unitary(g1, circ.n_gates, y))
+            start = s0
