@@ -50,6 +50,8 @@ def counting_qubits(N: int, eps: float) -> int:
     """Counting-register size for phase estimation that succeeds with
     probability at least 1 - eps: t = 2n + 1 + ceil(log2(2 + 1 / (2 eps))),
     n = ceil(log2 N) (Nielsen and Chuang, Eq. 5.35)."""
+    if not 0.0 < eps < 1.0:
+        raise ValueError("eps must lie in (0, 1)")
     n = max(1, math.ceil(math.log2(N)))
     return 2 * n + 1 + math.ceil(math.log2(2.0 + 1.0 / (2.0 * eps)))
 
@@ -103,6 +105,8 @@ class _Shor:
     def __init__(self, N: int, a: int, t: int):
         if N < 3 or not (1 < a < N) or math.gcd(a, N) != 1:
             raise ValueError("need N >= 3 and 1 < a < N coprime to N")
+        if t < 1:
+            raise ValueError("need at least one counting qubit")
         self.N, self.a, self.t = N, a, t
         self.n = n = max(1, math.ceil(math.log2(N)))
         self.c = list(range(t))

@@ -100,11 +100,15 @@ def test_qubit_counts_of_the_paper_instances():
     assert c.n_qubits == 2 + 2 * 4 + 2
 
 
-def test_rejects_bad_bases():
+def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
-        shor_circuit(15, 5, 2)
+        shor_circuit(15, 5, 2)      # gcd(5, 15) = 5
     with pytest.raises(ValueError):
         shor_circuit(15, 1, 2)
+    with pytest.raises(ValueError):
+        shor_circuit(15, 7, 0)
+    with pytest.raises(ValueError):
+        counting_qubits(15, 0.0)
 
 
 def test_cluster_tebd_oracle_reproduces_state(n15):
