@@ -20,6 +20,7 @@
  * Parity pins for every function live in tests/test_oracle_*.py.
  */
 #include <complex.h>
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -282,6 +283,14 @@ int orc_cluster_unitary(int q0, int k, int ng, const int *g5, const double *para
 /* ------------------------------------------------------------------------ */
 static void hestenes(int rows, int cols, cplx *A, cplx *V) {
   const double tol = 1e-15 * sqrt((double)(rows > 1 ? rows : 1));
+  /* A column whose norm is below eps * ||A||_F is a numerical zero: it adds */
+  /* at most that much to any singular value, and rotating against it is     */
+  /* meaningless.  Its inner products can be subnormal, and the phase        */
+  /* gamma / |gamma| of a subnormal gamma is not of unit modulus, which would */
+  /* make V non-unitary.  Such pairs are skipped.                            */
+  double fro = 0;
+  for (size_t i = 0; i < (size_t)rows * cols; i++) fro += creal(A[i]) * creal(A[i]) + cimag(A[i]) * cimag(A[i]);
+  const double zero2 = DBL_EPSILON * DBL_EPSILON * fro;
   for (int i = 0; i < cols * cols; i++) V[i] = 0;
   for (int i = 0; i < cols; i++) V[i * cols + i] = 1;
   for (int sweep = 0; sweep < 80; sweep++) {
@@ -297,7 +306,7 @@ static void hestenes(int rows, int cols, cplx *A, cplx *V) {
           gamma += conj(ap[i]) * aq[i];
         }
         double g = cabs(gamma);
-        if (g == 0.0 || g <= tol * sqrt(alpha * beta)) continue;
+        if (g == 0.0 || alpha <= zero2 || beta <= zero2 || g <= tol * sqrt(alpha * beta)) continue;
         rotated = 1;
         cplx ph = conj(gamma / g); /* e^{-i phi} */
         double zeta = (beta - alpha) / (2.0 * g);

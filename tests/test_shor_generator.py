@@ -11,7 +11,10 @@ pinned by number theory rather than by the oracle's own arithmetic:
   P(y) = sum_z |2^-t sum_{C : a^C = z mod N} exp(-2 pi i y C / 2^t)|^2;
 * every two-qubit gate acts on neighbours, as in the paper's SWAP routing;
 * the qubit counts of the paper's five instances (reading G18);
-* the oracle's cluster-TEBD reproduces the state vector on the N = 15 circuit."""
+* the oracle's cluster-TEBD and standard TEBD reproduce the state vector on
+  the N = 15 circuit.  The long standard-TEBD run (13 548 iterations) also
+  pins the oracle's one-sided Jacobi SVD on rank-deficient splits: a SWAP
+  split there produces columns of subnormal norm."""
 import math
 
 import numpy as np
@@ -119,3 +122,38 @@ def test_cluster_tebd_oracle_reproduces_state(n15):
     sv = m.statevector()
     assert abs(np.vdot(sv, psi)) / np.linalg.norm(sv) >= 1 - 1e-10
     assert m.logF == pytest.approx(0.0, abs=1e-12)
+
+
+def test_standard_tebd_oracle_reproduces_state(n15):
+    """Standard TEBD (one layer per iteration, two-qubit clusters) over all
+    13 548 layers of the N = 15 circuit."""
+    c, psi = n15
+    m = oracle.simulate(c, chi_max=64, cutoff=0.0, q_max=2 + 12, l_max=1, k_max=2)
+    sv = m.statevector()
+    assert abs(np.vdot(sv, psi)) / np.linalg.norm(sv) >= 1 - 1e-10
+    assert max(m.chi()) <= 4
+
+
+def test_oracle_svd_rank_deficient_split(n15):
+    """The split of the SWAP in layer 4380 of the N = 15 circuit (standard
+    TEBD): a 4 x 4 Schmidt-weighted matrix of rank 2.  Its singular values
+    against numpy's, and the right singular vectors orthonormal."""
+    c, _ = n15
+    layer, _ = oracle.asap_layers(c.n_qubits, c.gates)
+    sel = layer <= 4379
+    import synth
+    sub = synth.Circuit(c.n_qubits, c.gates[sel], c.params[sel])
+    m = oracle.simulate(sub, chi_max=64, cutoff=0.0, q_max=2 + 12, l_max=1, k_max=2)
+    swap = [(g, p) for g, p in zip(c.gates[layer == 4380], c.params[layer == 4380])]
+    assert len(swap) == 1 and swap[0][0][4] == synth.SWAP
+    q = int(min(swap[0][0][1], swap[0][0][2]))
+    th = np.einsum("asb,btc->astc", m.site(q), m.site(q + 1))
+    th = np.einsum("stuv,auvc->astc", oracle.gate_matrix(synth.SWAP).reshape(2, 2, 2, 2), th)
+    lam = m.lam(q)
+    M = (lam[:, None, None, None] * th).reshape(th.shape[0] * 2, -1)
+    s = np.zeros(min(M.shape))
+    Y = np.zeros(2 * M.shape[1] * len(s))
+    oracle._check(oracle._L().orc_svd(M.shape[0], M.shape[1], oracle._c128(M).reshape(-1), s, Y))
+    Y = Y.view(np.complex128).reshape(M.shape[1], len(s))
+    np.testing.assert_allclose(s, np.linalg.svd(M, compute_uv=False), atol=1e-14)
+    np.testing.assert_allclose(Y.conj().T @ Y, np.eye(len(s)), atol=1e-13)
