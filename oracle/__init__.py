@@ -222,6 +222,14 @@ def split_chain(theta: np.ndarray, lam_l: np.ndarray, chi_max: int, cutoff: floa
     return out
 
 
+def _positive_floor(floor: float):
+    """The numerical-zero floor of the truncation rule must be positive:
+    with none, singular values at the rounding level are kept, and their
+    singular vectors are not determined."""
+    if not floor > 0:
+        raise ValueError("floor must be positive (singular values <= floor * s_1 are numerical zeros)")
+
+
 # ---- MPS (Vidal form, Sec. II.B-II.C, III.A) --------------------------------
 class MPS:
     """Oracle MPS: right-canonical sites B_q (chi_q, 2, chi_{q+1}) + spectra."""
@@ -284,6 +292,7 @@ class MPS:
         _check(_L().orc_apply_1q(self._h, q, _c128(u).reshape(-1)))
 
     def cluster_update(self, q0, k, U, chi_max, cutoff, floor=1e-13):
+        _positive_floor(floor)
         f = np.zeros(max(k - 1, 1))
         r = np.zeros(max(k - 1, 1), dtype=np.int32)
         _check(_L().orc_cluster_update(self._h, q0, k, _c128(U).reshape(-1), int(chi_max),
@@ -291,6 +300,7 @@ class MPS:
         return f[: k - 1], r[: k - 1]
 
     def run(self, circ, chi_max, cutoff, q_max, l_max=0, k_max=0, floor=1e-13):
+        _positive_floor(floor)
         _check(_L().orc_run(self._h, circ.n_gates, _i32(circ.gates).reshape(-1),
                             np.ascontiguousarray(circ.params, dtype=np.float64), int(chi_max),
                             float(cutoff), int(q_max), int(l_max), int(k_max), float(floor)))

@@ -157,3 +157,9 @@ def test_oracle_svd_rank_deficient_split(n15):
     Y = Y.view(np.complex128).reshape(M.shape[1], len(s))
     np.testing.assert_allclose(s, np.linalg.svd(M, compute_uv=False), atol=1e-14)
     np.testing.assert_allclose(Y.conj().T @ Y, np.eye(len(s)), atol=1e-13)
+
+
+def test_oracle_rejects_zero_floor(n15):
+    c, _ = n15
+    with pytest.raises(ValueError):
+        oracle.simulate(c, chi_max=64, cutoff=0.0, q_max=14, l_max=1, k_max=2, floor=0.0)
