@@ -32,12 +32,15 @@ Quantum Inf. Comput. 3, 175 (2003)), restated:
   inverse QFT is applied to the counting qubits in reverse order, so that
   measuring c_(t-1-k) gives bit k of the phase estimate y ~ s 2^t / r.
 
-Routing (Sec. IV.B: long-range gates become chains of SWAP gates): the
-counting qubit of each controlled U_a is first moved next to the work
-register; every other two-qubit gate on qubits further apart moves its first
-qubit next to its second, applies the gate and moves it back.  Every move is
-a chain of nearest-neighbour SWAPs, and every qubit is back in place at the
-end, so the emitted circuit acts on the logical qubits in chain order.
+Routing (Sec. IV.B: long-range gates become chains of SWAP gates), two
+variants.  "return" (the default): the counting qubit of each controlled U_a
+is first moved next to the work register; every other two-qubit gate on
+qubits further apart moves its first qubit next to its second, applies the
+gate and moves it back.  Every qubit is back in place at the end, so the
+circuit acts on the logical qubits in chain order.  "lazy": the same moves
+without the returns; qubits end wherever the last gate left them, and
+``shor_build`` reports where each register ended.  Every move is a chain of
+nearest-neighbour SWAPs.
 """
 from __future__ import annotations
 
@@ -59,12 +62,13 @@ def counting_qubits(N: int, eps: float) -> int:
 class _Router:
     """Emits logical gates on a chain through nearest-neighbour SWAPs.
     pos[l] is the chain position of logical qubit l, at[p] the logical qubit
-    at position p."""
+    at position p.  lazy: a routed qubit stays where the gate needed it."""
 
-    def __init__(self, n: int):
+    def __init__(self, n: int, lazy: bool = False):
         self.b = _Builder(n)
         self.pos = list(range(n))
         self.at = list(range(n))
+        self.lazy = lazy
 
     def _swap(self, p: int):   # positions p and p + 1
         self.b.g2(SWAP, p, p + 1)
@@ -86,6 +90,8 @@ class _Router:
         return done
 
     def undo(self, done: list[int]):
+        if self.lazy:
+            return
         for p in reversed(done):
             self._swap(p)
 
@@ -102,7 +108,7 @@ class _Router:
 
 
 class _Shor:
-    def __init__(self, N: int, a: int, t: int):
+    def __init__(self, N: int, a: int, t: int, lazy: bool = False):
         if N < 3 or not (1 < a < N) or math.gcd(a, N) != 1:
             raise ValueError("need N >= 3 and 1 < a < N coprime to N")
         if t < 1:
@@ -113,7 +119,7 @@ class _Shor:
         self.x = list(range(t, t + n))
         self.bq = list(range(t + n, t + 2 * n + 1))       # n + 1 qubits, bq[0] least significant
         self.anc = t + 2 * n + 1
-        self.r = _Router(t + 2 * n + 2)
+        self.r = _Router(t + 2 * n + 2, lazy)
 
     # -- Fourier-basis arithmetic on b ------------------------------------
     def qft(self, qs, inverse=False):
@@ -206,7 +212,8 @@ class _Shor:
     def controlled_u(self, a, cj):
         """x <- a x mod N under control cj (b and the ancilla stay |0>)."""
         # bring the control next to the work register for the whole block
-        done = self.r.move(cj, self.r.pos[self.x[0]] - 1)
+        px = self.r.pos[self.x[0]]
+        done = self.r.move(cj, px - 1 if self.r.pos[cj] < px else px + 1)
         self.cmult(a, cj)
         for i in range(self.n):
             self.cswap(cj, self.x[i], self.bq[i])
@@ -224,12 +231,28 @@ class _Shor:
         return self.r.b.build()
 
 
-def shor_circuit(N: int, a: int, t: int | None = None, eps: float = 1e-3) -> Circuit:
+def shor_build(N: int, a: int, t: int | None = None, eps: float = 1e-3,
+               routing: str = "return") -> tuple[Circuit, dict]:
     """Order finding of a modulo N with t counting qubits (default from eps,
-    see ``counting_qubits``): t + 2n + 2 qubits, chain order counting register,
-    work register x (x_0 least significant), addition register b (b_0 least
-    significant), ancilla.  Nearest-neighbour gates only."""
-    return _Shor(N, a, counting_qubits(N, eps) if t is None else t).build()
+    see ``counting_qubits``): t + 2n + 2 qubits; nearest-neighbour gates only.
+    Returns the circuit and the chain positions its registers end at: "c"
+    (counting qubit c_j at c[j]), "x" (x_0 least significant), "b" (b_0
+    least significant), "anc".  With routing "return" they are the start
+    positions, in that order along the chain."""
+    if routing not in ("return", "lazy"):
+        raise ValueError("routing is 'return' or 'lazy'")
+    sh = _Shor(N, a, counting_qubits(N, eps) if t is None else t, lazy=routing == "lazy")
+    circ = sh.build()
+    pos = sh.r.pos
+    regs = {"c": [pos[q] for q in sh.c], "x": [pos[q] for q in sh.x], "b": [pos[q] for q in sh.bq],
+            "anc": pos[sh.anc]}
+    return circ, regs
+
+
+def shor_circuit(N: int, a: int, t: int | None = None, eps: float = 1e-3) -> Circuit:
+    """``shor_build`` with routing "return": chain order counting register,
+    work register x, addition register b, ancilla."""
+    return shor_build(N, a, t, eps)[0]
 
 
 def shor_registers(N: int, t: int) -> dict:

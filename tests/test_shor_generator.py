@@ -21,21 +21,33 @@ import numpy as np
 import pytest
 
 import oracle
-from synth.shor import counting_qubits, shor_circuit, shor_registers
+from synth.shor import counting_qubits, shor_build, shor_circuit, shor_registers
+
+
+def _bits_distribution(psi, n, positions, weights):
+    """Distribution of sum_j weights[j] * (bit at chain position positions[j])."""
+    p = np.abs(psi.reshape((2,) * n)) ** 2
+    pm = p.sum(axis=tuple(i for i in range(n) if i not in positions))
+    axes = sorted(positions)                       # pm's axes follow the chain order
+    out = {}
+    for idx in np.ndindex(*(2,) * len(axes)):
+        bit = dict(zip(axes, idx))
+        v = sum(w * bit[q] for q, w in zip(positions, weights))
+        out[v] = out.get(v, 0.0) + pm[idx]
+    return out
+
+
+def _counting_distribution(psi, n, cpos):
+    """P(y), y's bit k read from counting qubit c_(t-1-k) (at chain position
+    cpos[t-1-k])."""
+    t = len(cpos)
+    d = _bits_distribution(psi, n, cpos, [1 << (t - 1 - j) for j in range(t)])
+    return np.array([d.get(y, 0.0) for y in range(1 << t)])
 
 
 def _marginal(psi, n, qubits):
     p = np.abs(psi.reshape((2,) * n)) ** 2
     return p.sum(axis=tuple(i for i in range(n) if i not in qubits))
-
-
-def _counting_distribution(psi, n, t):
-    """P(y) with y's bit k read from counting qubit t - 1 - k."""
-    pc = _marginal(psi, n, list(range(t)))
-    out = np.zeros(1 << t)
-    for idx in np.ndindex(*(2,) * t):
-        out[sum(idx[t - 1 - k] << k for k in range(t))] += pc[idx]
-    return out
 
 
 @pytest.fixture(scope="module")
@@ -44,36 +56,44 @@ def n15():
     return c, oracle.statevector(c)
 
 
-def test_order_four_gives_exact_peaks(n15):
-    c, psi = n15
+@pytest.fixture(scope="module", params=["return", "lazy"])
+def n15_routed(request):
+    c, regs = shor_build(15, 7, 3, routing=request.param)
+    return c, regs, oracle.statevector(c)
+
+
+def test_order_four_gives_exact_peaks(n15_routed):
+    c, regs, psi = n15_routed
     t = 3
     assert c.n_qubits == t + 2 * 4 + 2
-    P = _counting_distribution(psi, c.n_qubits, t)
+    P = _counting_distribution(psi, c.n_qubits, regs["c"])
     expect = np.zeros(8)
     expect[[0, 2, 4, 6]] = 0.25
     np.testing.assert_allclose(P, expect, atol=1e-10)
 
 
-def test_work_register_and_ancillas(n15):
-    c, psi = n15
-    R = shor_registers(15, 3)
-    pb = _marginal(psi, c.n_qubits, R["b"] + [R["anc"]]).reshape(-1)
-    assert pb[0] == pytest.approx(1.0, abs=1e-10)
-    px = _marginal(psi, c.n_qubits, R["x"])
-    vals = {}
-    for idx in np.ndindex(*(2,) * len(R["x"])):
-        v = sum(idx[k] << k for k in range(len(R["x"])))   # x_0 least significant
-        if px[idx] > 1e-12:
-            vals[v] = px[idx]
+def test_work_register_and_ancillas(n15_routed):
+    c, regs, psi = n15_routed
+    n = c.n_qubits
+    zero = _bits_distribution(psi, n, regs["b"] + [regs["anc"]], [1 << k for k in range(len(regs["b"]) + 1)])
+    assert zero.get(0, 0.0) == pytest.approx(1.0, abs=1e-10)
+    x = _bits_distribution(psi, n, regs["x"], [1 << k for k in range(len(regs["x"]))])
+    vals = {v: p for v, p in x.items() if p > 1e-12}
     assert sorted(vals) == sorted({pow(7, k, 15) for k in range(4)})
     np.testing.assert_allclose(list(vals.values()), 0.25, atol=1e-10)
 
 
-def test_order_six_matches_closed_form():
+def test_return_routing_keeps_chain_order():
+    _, regs = shor_build(15, 7, 3)
+    assert regs == shor_registers(15, 3)
+
+
+@pytest.mark.parametrize("routing", ["return", "lazy"])
+def test_order_six_matches_closed_form(routing):
     N, a, t = 21, 2, 3
-    c = shor_circuit(N, a, t)
+    c, regs = shor_build(N, a, t, routing=routing)
     psi = oracle.statevector(c)
-    P = _counting_distribution(psi, c.n_qubits, t)
+    P = _counting_distribution(psi, c.n_qubits, regs["c"])
     C = np.arange(1 << t)
     z = np.array([pow(a, int(k), N) for k in C])
     ref = np.zeros(1 << t)
@@ -84,8 +104,8 @@ def test_order_six_matches_closed_form():
     np.testing.assert_allclose(P, ref, atol=1e-10)
 
 
-def test_nearest_neighbour_gates_only(n15):
-    c, _ = n15
+def test_nearest_neighbour_gates_only(n15_routed):
+    c, _, _ = n15_routed
     g = c.gates
     two = g[g[:, 0] == 2]
     assert len(two) > 0 and np.all(np.abs(two[:, 1] - two[:, 2]) == 1)
@@ -112,6 +132,8 @@ def test_rejects_bad_arguments():
         shor_circuit(15, 7, 0)
     with pytest.raises(ValueError):
         counting_qubits(15, 0.0)
+    with pytest.raises(ValueError):
+        shor_build(15, 7, 2, routing="greedy")
 
 
 def test_cluster_tebd_oracle_reproduces_state(n15):
