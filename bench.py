@@ -729,13 +729,14 @@ def run_shor(args):
     import torch
 
     import paper_2502_19289_gb300 as P
-    from synth.shor import counting_qubits, shor_circuit
+    from synth.shor import counting_qubits, shor_build, shor_circuit
     eps = {15: 1e-3, 21: 1e-4, 35: 1e-5, 91: 1e-5, 221: 1e-9}
     N, a = args.shor_n, args.shor_a
     t = args.shor_t if args.shor_t > 0 else counting_qubits(N, eps.get(N, 1e-3))
     chi, k_max, cut = args.chi, args.kmax, 1e-8
     lg = int(math.log2(chi))
-    c = shor_circuit(N, a, t)
+    c, regs = shor_build(N, a, t, routing=args.shor_routing)
+    cpos = regs["c"]   # chain position of counting qubit c_j
     n = c.n_qubits
     circ = P.Circuit(n, c.gates, c.params)
     stream = torch.cuda.Stream()
@@ -764,10 +765,12 @@ def run_shor(args):
             s = mps.site(q)
             v = np.einsum("ia,asb->isb", v, s).reshape(-1, s.shape[2])
         p = np.abs(v.reshape((2,) * n)) ** 2
-        pc = p.sum(axis=tuple(range(t, n)))
+        pc = p.sum(axis=tuple(i for i in range(n) if i not in cpos))   # axes in chain order
+        axes = sorted(cpos)
         got = np.zeros(1 << t)
         for idx in np.ndindex(*(2,) * t):
-            got[sum(idx[t - 1 - k] << k for k in range(t))] += pc[idx]
+            bit = dict(zip(axes, idx))
+            got[sum(bit[cpos[t - 1 - k]] << k for k in range(t))] += pc[idx]
         C = np.arange(1 << t)
         z = np.array([pow(a, int(k), N) for k in C])
         ref = np.array([sum(abs(np.exp(-2j * np.pi * y * C[z == u] / (1 << t)).sum() / (1 << t)) ** 2
@@ -789,6 +792,7 @@ def run_shor(args):
                       "higher_is_better": True, "n_gpus": 1, "dtype": "c64",
                       "data": "synthetic (Beauregard's order-finding circuit, SWAP-routed; from |0...0>)",
                       "config": {"workload": f"Shor order finding N={N}, a={a}, t={t} counting qubits, {n} qubits, "
+                                             f"{args.shor_routing} routing, "
                                              f"{circ.n_gates} gates in {circ.n_layers} layers; chi_max={chi}, cutoff "
                                              f"1e-8; cluster-TEBD k_max={k_max}, Q_max={3 + 2 * lg}; standard TEBD "
                                              "L_max=1, k_max=2",
@@ -1153,6 +1157,8 @@ def main():
     ap.add_argument("--shor-a", type=int, default=2, help="shor: the base (coprime with N)")
     ap.add_argument("--shor-t", type=int, default=0,
                     help="shor: counting qubits (default: phase-estimation size for the paper's precision)")
+    ap.add_argument("--shor-routing", default="return", choices=["return", "lazy"],
+                    help="shor: SWAP routing (return: every routed qubit moves back; lazy: it stays)")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="tensor-core policy (default 1, the size policy; 0 never; 2 always, "
                          "including the Jacobi round updates)")
